@@ -1,0 +1,130 @@
+/*
+ * lb.h — C ABI of the GB300 (sm_103a) two-belt Shan–Chen lattice Boltzmann
+ * library (liblbsc.so).
+ *
+ * The method is the one of Chibbaro, Falcucci, Chen, Shan, Chiatti, Succi,
+ * "Lattice Boltzmann models for non-ideal fluids with arrested
+ * phase-separation" (arXiv:1008.2865): a periodic 2D D2Q9 BGK fluid (Sec. 2,
+ * Eqs. 1-4) with the Shan–Chen pseudopotential psi(rho) (Sec. 2) acting
+ * through a two-belt, 24-neighbour force (Sec. 3, Eq. FORCE and Table 1),
+ * plus the Ising-like pseudo-energies E_s, E_m and E_bulk of Sec. 5.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an lb_status; the library never aborts, traps or
+ *     prints. After LB_ERR_CUDA the state is poisoned: only lb_destroy (and
+ *     lb_time) remain valid on it.
+ *   - Fields are row-major [y][x] (x fastest), N = nx*ny doubles.
+ *   - Inputs are copied; outputs go to caller-owned memory. Pointers may be
+ *     host memory (pageable or pinned) or device memory of the state's
+ *     device; the library tells them apart with cudaPointerGetAttributes.
+ *   - The library owns the device memory of a state (allocated in lb_init,
+ *     freed in lb_destroy). There is no global mutable state: several states
+ *     may live on one device and be driven from different host threads, one
+ *     thread per state at a time.
+ *   - Work is enqueued on the stream given at init (a cudaStream_t, or NULL
+ *     for the legacy default stream) on the device named in lb_params.device.
+ *     lb_step is asynchronous; lb_energy, lb_fields and lb_trace synchronise
+ *     that stream before they return.
+ */
+#ifndef LBSC_LB_H
+#define LBSC_LB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = -1,        /* invalid argument; nothing was changed */
+    LB_ERR_CUDA = -2,       /* a CUDA call failed; the state is poisoned */
+    LB_ERR_OOM = -3,        /* device allocation failed; nothing was created */
+    LB_ERR_NONFINITE = -4,  /* the lattice holds a NaN/Inf density or energy */
+    LB_ERR_STATE = -5       /* call not valid in the state's current condition */
+} lb_status;
+
+/* Pseudopotential form. Sec. 2: psi = sqrt(rho0) (1 - exp(-rho/rho0)),
+ * the Shan–Chen form the paper uses throughout (rho0 = 1 in Sec. 3). */
+typedef enum { LB_PSI_SC_EXP = 0 } lb_psi_form;
+
+/* Arithmetic of a state.
+ *   LB_FP32: the throughput path. Populations are stored in FP32 as
+ *            deviations g_i = f*_i - w_i rho_ref from the rest equilibrium at
+ *            the reference density rho_ref, psi as psi - psi(rho_ref); all
+ *            arithmetic is FP32 except the FP64 energy/mass accumulation.
+ *   LB_FP64: the parity path: FP64 populations and arithmetic in the same
+ *            operation order as a plain per-site evaluation of Eqs. 1-4 and
+ *            Eq. FORCE, without fused multiply-add, with a correctly rounded
+ *            exp; slow on GB300 and not meant for throughput.
+ *   LB_FP16_DELTA: as LB_FP32 but g_i stored in IEEE half precision (FP32
+ *            arithmetic, FP32 psi). */
+typedef enum { LB_FP32 = 0, LB_FP64 = 1, LB_FP16_DELTA = 2 } lb_precision;
+
+typedef struct {
+    int nx, ny;             /* lattice size; both >= 5 (the force stencil reaches 2 sites) */
+    double omega;           /* BGK relaxation frequency 1/tau, 0 < omega < 2 (Eq. 1; tau = 1 in Sec. 4) */
+    double G1;              /* first-belt coupling on the D2Q9 weights w_i (Eq. FORCE); < 0 attracts */
+    double G2;              /* coupling on the E(8) weights p of belts 1 and 2 (Eq. FORCE, Table 1) */
+    double rho0;            /* psi density scale rho0 > 0 (Sec. 2) */
+    lb_psi_form psi_form;   /* LB_PSI_SC_EXP */
+    lb_precision prec;      /* arithmetic, see above */
+    int trace_every;        /* record (t, mass, E_s, E_m, E_bulk) every this many steps; 0 = never */
+    double rho_ref;         /* FP32/FP16 storage reference density; <= 0 means the mean of rho_init */
+    int device;             /* CUDA device ordinal the state lives on */
+} lb_params;
+
+typedef struct lb_state lb_state;   /* opaque; owns device memory */
+
+/* Create a state at t = 0 with f_i(x, 0) = w_i rho_init(x), the u = 0
+ * equilibrium of Eq. 4 (the noisy-density start of Sec. 4).
+ *   out       receives the new state (set to NULL on failure)
+ *   p         parameters; validated: nx, ny >= 5, 0 < omega < 2, finite G1
+ *             and G2, rho0 > 0, trace_every >= 0, known psi_form and prec,
+ *             nx*ny*9 below 2^31
+ *   rho_init  N initial densities, host or device, each finite and > 0
+ *   stream    cudaStream_t (as void*) used by every later call on the state
+ * Errors: LB_ERR_ARG (bad parameter or rho_init), LB_ERR_OOM, LB_ERR_CUDA. */
+lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, void* stream);
+
+/* Advance n >= 0 steps of Eq. 1: psi(rho) (Sec. 2), the two-belt force of
+ * Eq. FORCE taken with the attractive sign of Eq. forza, BGK collision
+ * towards the Eq. 4 equilibrium at the shifted velocity u + F/(omega rho),
+ * then streaming. States t with t % trace_every == 0 append a trace row.
+ * Asynchronous. Errors: LB_ERR_ARG (n < 0), LB_ERR_STATE, LB_ERR_CUDA. */
+lb_status lb_step(lb_state* s, long n);
+
+/* Pseudo-energies and mass of the current state t (Sec. 5):
+ *   out[0] = E_s    = 1/2 sum_x psi(x) sum_{i=0..8} (G1 w_i + G2 p_si) psi(x + c_i)
+ *   out[1] = E_m    = 1/2 sum_x psi(x) sum_{i=1..16} G2 p_mi psi(x + c_mi)
+ *   out[2] = E_bulk = (G1 + G2)/2 sum_x psi(x)^2                (Eq. Ebulk)
+ *   out[3] = mass   = sum_x rho(x)
+ * out is host memory (4 doubles). Synchronises the stream.
+ * Errors: LB_ERR_ARG, LB_ERR_NONFINITE (any of the four is not finite),
+ * LB_ERR_STATE, LB_ERR_CUDA. */
+lb_status lb_energy(lb_state* s, double out[4]);
+
+/* Density rho = sum f_i and velocity u = sum c_i f_i / rho (Eqs. 2-3) of the
+ * current state, written as N doubles each into caller-owned host or device
+ * arrays; any of the three may be NULL. Synchronises the stream.
+ * Errors: LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA. */
+lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy);
+
+/* Copy the recorded trace rows (t, mass, E_s, E_m, E_bulk), oldest first,
+ * into buf (host, cap rows of 5 doubles); *count receives the number of rows
+ * written (the most recent ones if more than cap are stored; the device ring
+ * keeps the last 65536). Synchronises the stream.
+ * Errors: LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA. */
+lb_status lb_trace(lb_state* s, double* buf, int cap, int* count);
+
+/* Current time step t (number of lb_step steps taken since lb_init); -1 for NULL. */
+long lb_time(const lb_state* s);
+
+/* Free the state and its device memory; NULL is a no-op. Synchronises the stream. */
+void lb_destroy(lb_state* s);
+
+/* Static description of a status code. */
+const char* lb_status_str(lb_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
