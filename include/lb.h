@@ -115,6 +115,16 @@ lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy);
  * Errors: LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA. */
 lb_status lb_trace(lb_state* s, double* buf, int cap, int* count);
 
+/* Launch shape of the fused FP32/FP16 step kernel: CTAs of block_x threads
+ * cover block_x - 2 output columns (one halo column each side) and
+ * rows_per_cta output rows. lb_set_launch accepts block_x in
+ * {64, 96, 128, 192, 256} and rows_per_cta in [16, 4096]; it changes only how
+ * the work is split, not the result beyond FP32 rounding of the energy
+ * partial sums. Both return LB_ERR_ARG for NULL or out-of-range arguments and
+ * LB_ERR_STATE for an FP64 state (whose kernels have no such shape). */
+lb_status lb_get_launch(const lb_state* s, int* block_x, int* rows_per_cta);
+lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta);
+
 /* Current time step t (number of lb_step steps taken since lb_init); -1 for NULL. */
 long lb_time(const lb_state* s);
 

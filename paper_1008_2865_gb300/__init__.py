@@ -1,0 +1,85 @@
+"""GB300-native two-belt Shan–Chen lattice Boltzmann (Chibbaro et al., arXiv:1008.2865).
+
+The compute path is liblbsc.so (CUDA, sm_103a) behind the C ABI of
+include/lb.h; :mod:`paper_1008_2865_gb300.capi` binds it with ctypes under the
+same names, and :class:`Lattice` wraps one state. PyTorch, when used, only
+supplies device memory and the CUDA stream.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import capi, inputs  # noqa: F401
+from .capi import (LBError, lb_destroy, lb_energy, lb_fields, lb_get_launch,  # noqa: F401
+                   lb_init, lb_set_launch, lb_status_str, lb_step, lb_time, lb_trace,
+                   make_params)
+
+
+def couplings_from_A(A1: float, A2: float, lam: float = 1.5):
+    """(G1, G2) from the Sec. 4 parameters A1 = G1 + G2 and A2 = G1 + lam G2 (lam = 3/2)."""
+    G2 = (A2 - A1) / (lam - 1.0)
+    return A1 - G2, G2
+
+
+class Lattice:
+    """One periodic lattice on the GPU.
+
+    >>> lat = Lattice(rho_init, G1=-5.0, G2=0.6)        # rho_init: [ny, nx] float64
+    >>> lat.step(100); E_s, E_m, E_bulk, mass = lat.energy()
+    """
+
+    def __init__(self, rho_init, omega=1.0, G1=-5.0, G2=0.0, rho0=1.0, prec="fp32",
+                 trace_every=10, rho_ref=0.0, device=0, stream=0):
+        ny, nx = rho_init.shape
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = make_params(nx, ny, omega, G1, G2, rho0, prec, trace_every, rho_ref, device)
+        self.handle = lb_init(self.params, rho_init, stream)
+
+    def step(self, n: int = 1) -> None:
+        lb_step(self.handle, n)
+
+    @property
+    def t(self) -> int:
+        return lb_time(self.handle)
+
+    def energy(self):
+        return lb_energy(self.handle)
+
+    def fields(self, rho=None, ux=None, uy=None):
+        """Fill the given [ny, nx] float64 arrays/tensors; with none given, return NumPy arrays."""
+        if rho is None and ux is None and uy is None:
+            rho = np.empty((self.ny, self.nx))
+            ux = np.empty((self.ny, self.nx))
+            uy = np.empty((self.ny, self.nx))
+            lb_fields(self.handle, rho, ux, uy)
+            return rho, ux, uy
+        lb_fields(self.handle, rho, ux, uy)
+        return rho, ux, uy
+
+    @property
+    def launch(self):
+        """(block_x, rows_per_cta) of the fused step kernel."""
+        return lb_get_launch(self.handle)
+
+    def set_launch(self, block_x: int, rows_per_cta: int) -> None:
+        lb_set_launch(self.handle, block_x, rows_per_cta)
+
+    def trace(self, cap: int = 65536):
+        return lb_trace(self.handle, cap)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

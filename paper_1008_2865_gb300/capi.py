@@ -1,0 +1,178 @@
+"""ctypes binding of liblbsc.so — the functions of include/lb.h under the same names.
+
+Argument marshalling only: every step of the lattice Boltzmann update runs in
+the library's CUDA kernels. There is no fallback: if the shared library is
+missing or cannot be loaded, every call raises.
+
+Pointers may be NumPy arrays (host memory) or anything exposing
+``data_ptr()`` (torch tensors on the state's device). Streams are passed as
+the integer handle ``torch.cuda.Stream.cuda_stream`` (0 = legacy default).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_OOM, LB_ERR_NONFINITE, LB_ERR_STATE = 0, -1, -2, -3, -4, -5
+LB_PSI_SC_EXP = 0
+LB_FP32, LB_FP64, LB_FP16_DELTA = 0, 1, 2
+
+_PRECISION = {"fp32": LB_FP32, "fp64": LB_FP64, "fp16_delta": LB_FP16_DELTA}
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("omega", ctypes.c_double), ("G1", ctypes.c_double), ("G2", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("psi_form", ctypes.c_int), ("prec", ctypes.c_int), ("trace_every", ctypes.c_int),
+        ("rho_ref", ctypes.c_double), ("device", ctypes.c_int),
+    ]
+
+
+class LBError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {lb_status_str(status)} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load liblbsc.so (building it first only when asked)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(
+                        f"{path} is missing: build it with paper_1008_2865_gb300.build.build()")
+                _build.build()
+            lib = ctypes.CDLL(path)
+            vp = ctypes.c_void_p
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.lb_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(lb_params), vp, vp]
+            lib.lb_init.restype = ctypes.c_int
+            lib.lb_step.argtypes = [vp, ctypes.c_long]
+            lib.lb_step.restype = ctypes.c_int
+            lib.lb_energy.argtypes = [vp, dp]
+            lib.lb_energy.restype = ctypes.c_int
+            lib.lb_fields.argtypes = [vp, vp, vp, vp]
+            lib.lb_fields.restype = ctypes.c_int
+            lib.lb_trace.argtypes = [vp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+            lib.lb_trace.restype = ctypes.c_int
+            lib.lb_time.argtypes = [vp]
+            lib.lb_time.restype = ctypes.c_long
+            ip = ctypes.POINTER(ctypes.c_int)
+            lib.lb_get_launch.argtypes = [vp, ip, ip]
+            lib.lb_get_launch.restype = ctypes.c_int
+            lib.lb_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            lib.lb_set_launch.restype = ctypes.c_int
+            lib.lb_destroy.argtypes = [vp]
+            lib.lb_destroy.restype = None
+            lib.lb_status_str.argtypes = [ctypes.c_int]
+            lib.lb_status_str.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    """Raw address of a NumPy array / torch tensor / int / None."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"cannot pass {type(a)!r} as a pointer")
+
+
+def _check(st: int, where: str):
+    if st != LB_OK:
+        raise LBError(st, where)
+
+
+def make_params(nx, ny, omega=1.0, G1=-5.0, G2=0.0, rho0=1.0, prec="fp32", trace_every=10,
+                rho_ref=0.0, device=0, psi_form=LB_PSI_SC_EXP) -> lb_params:
+    return lb_params(int(nx), int(ny), float(omega), float(G1), float(G2), float(rho0),
+                     int(psi_form), _PRECISION.get(prec, prec), int(trace_every),
+                     float(rho_ref), int(device))
+
+
+def lb_status_str(st: int) -> str:
+    return load().lb_status_str(int(st)).decode()
+
+
+def lb_init(params: lb_params, rho_init, stream: int = 0) -> int:
+    """Returns the opaque state handle (an int). rho_init: [ny, nx] float64, host or device."""
+    if isinstance(rho_init, np.ndarray):
+        rho_init = np.ascontiguousarray(rho_init, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(load().lb_init(ctypes.byref(h), ctypes.byref(params), _ptr(rho_init),
+                          ctypes.c_void_p(stream or None)), "lb_init")
+    return h.value
+
+
+def lb_step(h: int, n: int) -> None:
+    _check(load().lb_step(ctypes.c_void_p(h), int(n)), "lb_step")
+
+
+def lb_energy(h: int):
+    """(E_s, E_m, E_bulk, mass) of the current state."""
+    out = (ctypes.c_double * 4)()
+    st = load().lb_energy(ctypes.c_void_p(h), out)
+    if st not in (LB_OK, LB_ERR_NONFINITE):
+        raise LBError(st, "lb_energy")
+    vals = tuple(out)
+    if st == LB_ERR_NONFINITE:
+        raise LBError(st, f"lb_energy {vals}")
+    return vals
+
+
+def lb_fields(h: int, rho=None, ux=None, uy=None) -> None:
+    _check(load().lb_fields(ctypes.c_void_p(h), _ptr(rho), _ptr(ux), _ptr(uy)), "lb_fields")
+
+
+def lb_trace(h: int, cap: int = 65536) -> np.ndarray:
+    buf = np.zeros((max(cap, 1), 5))
+    cnt = ctypes.c_int(0)
+    _check(load().lb_trace(ctypes.c_void_p(h), buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           int(cap), ctypes.byref(cnt)), "lb_trace")
+    return buf[: cnt.value].copy()
+
+
+def lb_get_launch(h: int):
+    """(block_x, rows_per_cta) of the fused step kernel."""
+    bx, rows = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().lb_get_launch(ctypes.c_void_p(h), ctypes.byref(bx), ctypes.byref(rows)),
+           "lb_get_launch")
+    return bx.value, rows.value
+
+
+def lb_set_launch(h: int, block_x: int, rows_per_cta: int) -> None:
+    _check(load().lb_set_launch(ctypes.c_void_p(h), int(block_x), int(rows_per_cta)),
+           "lb_set_launch")
+
+
+def lb_time(h) -> int:
+    return int(load().lb_time(ctypes.c_void_p(h)))
+
+
+def lb_destroy(h) -> None:
+    load().lb_destroy(ctypes.c_void_p(h))

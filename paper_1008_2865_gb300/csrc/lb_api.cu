@@ -1,0 +1,465 @@
+// lb_api.cu — the C ABI of liblbsc.so (include/lb.h): parameter validation,
+// device memory of a state, launch sequencing on the caller's stream, and
+// host<->device transfers at the boundary.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "lb_internal.h"
+
+using namespace lbsc;
+
+namespace lbsc {
+
+Couplings couplings(double G1, double G2)
+{
+    // Table 1 weights; p_s0 = 1 - sum of the 24 link weights (Eq. weights_1)
+    const double p1 = 4.0 / 63.0, p2 = 4.0 / 135.0, p4 = 1.0 / 180.0, p5 = 2.0 / 945.0,
+                 p8 = 1.0 / 15120.0;
+    const double p0 = 1.0 - (4 * p1 + 4 * p2 + 4 * p4 + 8 * p5 + 4 * p8);
+    Couplings c;
+    c.K0 = G1 * (4.0 / 9.0) + G2 * p0;
+    c.K1 = G1 * (1.0 / 9.0) + G2 * p1;
+    c.K2 = G1 * (1.0 / 36.0) + G2 * p2;
+    c.K4 = G2 * p4;
+    c.K5 = G2 * p5;
+    c.K8 = G2 * p8;
+    return c;
+}
+
+}  // namespace lbsc
+
+struct lb_state {
+    lb_params p;
+    cudaStream_t stream = nullptr;
+    long long t = 0;
+    bool poisoned = false;
+    long long N = 0;
+    // FP32 / FP16 deviation storage
+    void* g[2] = {nullptr, nullptr};
+    float* dpsi[2] = {nullptr, nullptr};
+    int cur = 0;
+    double rho_ref = 0.0;
+    Fp32Launch launch{128, 64};
+    // FP64 parity storage
+    double* f64[2] = {nullptr, nullptr};
+    double* psi64 = nullptr;
+    double* rho64 = nullptr;
+    // reductions, trace, scratch
+    double* partials = nullptr;
+    size_t partials_cap = 0;       // number of 4-double partials
+    unsigned int* counter = nullptr;
+    double* trace = nullptr;
+    int* trace_count = nullptr;
+    double* res = nullptr;         // 4 doubles of results
+    int* flag = nullptr;
+    double* field_tmp = nullptr;   // N doubles, allocated on the first host-destined lb_fields
+};
+
+namespace {
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+lb_status validate(const lb_params* p)
+{
+    if (!p) return LB_ERR_ARG;
+    if (p->nx < 5 || p->ny < 5) return LB_ERR_ARG;
+    if ((long long)p->nx * p->ny * 9 >= (1LL << 31)) return LB_ERR_ARG;
+    if (!(p->omega > 0.0 && p->omega < 2.0)) return LB_ERR_ARG;
+    if (!std::isfinite(p->G1) || !std::isfinite(p->G2)) return LB_ERR_ARG;
+    if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return LB_ERR_ARG;
+    if (p->psi_form != LB_PSI_SC_EXP) return LB_ERR_ARG;
+    if (p->prec != LB_FP32 && p->prec != LB_FP64 && p->prec != LB_FP16_DELTA) return LB_ERR_ARG;
+    if (p->trace_every < 0) return LB_ERR_ARG;
+    if (!std::isfinite(p->rho_ref)) return LB_ERR_ARG;
+    if (p->device < 0) return LB_ERR_ARG;
+    return LB_OK;
+}
+
+// Default launch shape: 128-thread strips, rows chosen for about four waves
+// of 8 resident CTAs per SM on a 152-SM part, at least 16 rows.
+Fp32Launch default_launch(int nx, int ny)
+{
+    Fp32Launch L{128, 64};
+    const long long strips = (nx + L.block_x - 3) / (L.block_x - 2);
+    const long long target = 152LL * 8 * 4;
+    long long rows = (strips * ny + target - 1) / target;
+    if (rows < 16) rows = 16;
+    if (rows > 512) rows = 512;
+    L.rows = (int)rows;
+    return L;
+}
+
+size_t elem_size(lb_precision p) { return p == LB_FP16_DELTA ? 2 : 4; }
+
+template <typename T>
+StepArgs<T> make_args(const lb_state* s)
+{
+    const lb_params& p = s->p;
+    const Couplings K = couplings(p.G1, p.G2);
+    StepArgs<T> a{};
+    a.g_in = static_cast<const T*>(s->g[s->cur]);
+    a.g_out = static_cast<T*>(s->g[s->cur ^ 1]);
+    a.dpsi_in = s->dpsi[s->cur];
+    a.dpsi_out = s->dpsi[s->cur ^ 1];
+    a.nx = p.nx;
+    a.ny = p.ny;
+    a.rows = s->launch.rows;
+    a.N = s->N;
+    a.omega = (float)p.omega;
+    a.omc = (float)(1.0 - p.omega);
+    a.inv_omega = (float)(1.0 / p.omega);
+    a.w0 = (float)(4.0 / 9.0);
+    a.w1 = (float)(1.0 / 9.0);
+    a.w2 = (float)(1.0 / 36.0);
+    a.K0 = (float)K.K0;
+    a.K1 = (float)K.K1;
+    a.K2 = (float)K.K2;
+    a.K4 = (float)K.K4;
+    a.K5 = (float)K.K5;
+    a.K8 = (float)K.K8;
+    a.rho_ref = (float)s->rho_ref;
+    a.psi_ref = (float)(std::sqrt(p.rho0) * -std::expm1(-s->rho_ref / p.rho0));
+    a.cpsi = (float)(-std::sqrt(p.rho0) * std::exp(-s->rho_ref / p.rho0));
+    a.inv_rho0 = (float)(1.0 / p.rho0);
+    a.half_A1 = (float)(0.5 * (p.G1 + p.G2));
+    a.partials = s->partials;
+    a.counter = s->counter;
+    a.trace = s->trace;
+    a.trace_count = s->trace_count;
+    a.t = s->t;
+    return a;
+}
+
+lb_status fail_cuda(lb_state* s)
+{
+    if (s) s->poisoned = true;
+    cudaGetLastError();
+    return LB_ERR_CUDA;
+}
+
+#define LB_CUDA(s, call)                          \
+    do {                                          \
+        if ((call) != cudaSuccess) return fail_cuda(s); \
+    } while (0)
+
+void free_state(lb_state* s)
+{
+    if (!s) return;
+    cudaSetDevice(s->p.device);
+    cudaStreamSynchronize(s->stream);
+    void* ptrs[] = {s->g[0], s->g[1], s->dpsi[0], s->dpsi[1], s->f64[0], s->f64[1], s->psi64,
+                    s->rho64, s->partials, s->counter, s->trace, s->trace_count, s->res,
+                    s->flag, s->field_tmp};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    cudaGetLastError();
+    delete s;
+}
+
+lb_status step_fp32(lb_state* s, long n)
+{
+    for (long k = 0; k < n; ++k) {
+        const bool reduce = s->p.trace_every > 0 && (s->t % s->p.trace_every) == 0;
+        cudaError_t e;
+        if (s->p.prec == LB_FP32)
+            e = fp32_step(make_args<float>(s), s->launch, reduce, s->stream);
+        else
+            e = fp16_step(make_args<__half>(s), s->launch, reduce, s->stream);
+        if (e != cudaSuccess) return fail_cuda(s);
+        s->cur ^= 1;
+        s->t += 1;
+    }
+    return LB_OK;
+}
+
+Fp64Args make64(const lb_state* s)
+{
+    Fp64Args a;
+    a.f_in = s->f64[s->cur];
+    a.f_out = s->f64[s->cur ^ 1];
+    a.psi = s->psi64;
+    a.rho = s->rho64;
+    a.nx = s->p.nx;
+    a.ny = s->p.ny;
+    a.omega = s->p.omega;
+    a.G1 = s->p.G1;
+    a.G2 = s->p.G2;
+    a.rho0 = s->p.rho0;
+    return a;
+}
+
+lb_status step_fp64(lb_state* s, long n)
+{
+    for (long k = 0; k < n; ++k) {
+        const Fp64Args a = make64(s);
+        LB_CUDA(s, fp64_psi(a, s->stream));
+        if (s->p.trace_every > 0 && (s->t % s->p.trace_every) == 0)
+            LB_CUDA(s, fp64_energy(a, s->partials, s->counter, s->res, s->trace, s->trace_count,
+                                   s->t, s->stream));
+        LB_CUDA(s, fp64_collide_stream(a, s->stream));
+        s->cur ^= 1;
+        s->t += 1;
+    }
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_status_str(lb_status st)
+{
+    switch (st) {
+    case LB_OK: return "ok";
+    case LB_ERR_ARG: return "invalid argument";
+    case LB_ERR_CUDA: return "CUDA error (state poisoned)";
+    case LB_ERR_OOM: return "device allocation failed";
+    case LB_ERR_NONFINITE: return "non-finite density or energy";
+    case LB_ERR_STATE: return "call not valid in the current state";
+    }
+    return "unknown status";
+}
+
+lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, void* stream)
+{
+    if (!out) return LB_ERR_ARG;
+    *out = nullptr;
+    if (validate(p) != LB_OK || !rho_init) return LB_ERR_ARG;
+    lb_state* s = new (std::nothrow) lb_state();
+    if (!s) return LB_ERR_OOM;
+    s->p = *p;
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->N = (long long)p->nx * p->ny;
+    const long long N = s->N;
+    if (cudaSetDevice(p->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return LB_ERR_CUDA;
+    }
+    auto alloc = [&](void** q, size_t bytes) -> bool {
+        if (cudaMalloc(q, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    };
+    s->launch = default_launch(p->nx, p->ny);
+    const size_t nblk_step = (size_t)fp32_grid_blocks(p->nx, p->ny, Fp32Launch{64, 16});
+    s->partials_cap = nblk_step > 152 * 16 ? nblk_step : 152 * 16;
+    bool ok = alloc((void**)&s->partials, 4 * sizeof(double) * s->partials_cap) &&
+              alloc((void**)&s->counter, sizeof(unsigned int)) &&
+              alloc((void**)&s->trace, sizeof(double) * kTraceCap * kTraceCols) &&
+              alloc((void**)&s->trace_count, sizeof(int)) &&
+              alloc((void**)&s->res, 4 * sizeof(double)) && alloc((void**)&s->flag, sizeof(int));
+    if (ok && p->prec == LB_FP64) {
+        ok = alloc((void**)&s->f64[0], 9 * sizeof(double) * N) &&
+             alloc((void**)&s->f64[1], 9 * sizeof(double) * N) &&
+             alloc((void**)&s->psi64, sizeof(double) * N) &&
+             alloc((void**)&s->rho64, sizeof(double) * N);
+    } else if (ok) {
+        const size_t es = elem_size(p->prec);
+        ok = alloc(&s->g[0], 9 * es * N) && alloc(&s->g[1], 9 * es * N) &&
+             alloc((void**)&s->dpsi[0], sizeof(float) * N) &&
+             alloc((void**)&s->dpsi[1], sizeof(float) * N);
+    }
+    if (!ok) {
+        free_state(s);
+        return LB_ERR_OOM;
+    }
+    // rho_init on the device (copied when it is host memory)
+    double* rho_dev = nullptr;
+    const bool dev_src = is_device_ptr(rho_init);
+    if (!alloc((void**)&rho_dev, sizeof(double) * N)) {
+        free_state(s);
+        return LB_ERR_OOM;
+    }
+    auto bail = [&](lb_status st) {
+        cudaFree(rho_dev);
+        cudaGetLastError();
+        free_state(s);
+        return st;
+    };
+    if (cudaMemcpyAsync(rho_dev, rho_init, sizeof(double) * N,
+                        dev_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->counter, 0, sizeof(unsigned int), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->trace_count, 0, sizeof(int), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream) != cudaSuccess)
+        return bail(LB_ERR_CUDA);
+    if (rho_check_sum(rho_dev, N, s->partials, s->counter, s->res, s->flag, s->stream) !=
+        cudaSuccess)
+        return bail(LB_ERR_CUDA);
+    double sum = 0.0;
+    int flag = 0;
+    if (cudaMemcpyAsync(&sum, s->res, sizeof(double), cudaMemcpyDeviceToHost, s->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return bail(LB_ERR_CUDA);
+    if (flag) return bail(LB_ERR_ARG);
+    s->rho_ref = p->rho_ref > 0.0 ? p->rho_ref : sum / (double)N;
+    cudaError_t e;
+    if (p->prec == LB_FP64)
+        e = fp64_init(s->f64[0], rho_dev, p->nx, p->ny, s->stream);
+    else if (p->prec == LB_FP32)
+        e = delta_init<float>(static_cast<float*>(s->g[0]), s->dpsi[0], rho_dev, p->nx, p->ny,
+                              s->rho_ref, p->rho0, s->stream);
+    else
+        e = delta_init<__half>(static_cast<__half*>(s->g[0]), s->dpsi[0], rho_dev, p->nx, p->ny,
+                               s->rho_ref, p->rho0, s->stream);
+    if (e != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return bail(LB_ERR_CUDA);
+    cudaFree(rho_dev);
+    *out = s;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_state* s, long n)
+{
+    if (!s || n < 0) return LB_ERR_ARG;
+    if (s->poisoned) return LB_ERR_STATE;
+    if (n == 0) return LB_OK;
+    LB_CUDA(s, cudaSetDevice(s->p.device));
+    return s->p.prec == LB_FP64 ? step_fp64(s, n) : step_fp32(s, n);
+}
+
+lb_status lb_energy(lb_state* s, double out[4])
+{
+    if (!s || !out) return LB_ERR_ARG;
+    if (s->poisoned) return LB_ERR_STATE;
+    LB_CUDA(s, cudaSetDevice(s->p.device));
+    if (s->p.prec == LB_FP64) {
+        const Fp64Args a = make64(s);
+        LB_CUDA(s, fp64_psi(a, s->stream));
+        LB_CUDA(s, fp64_energy(a, s->partials, s->counter, s->res, nullptr, nullptr, s->t,
+                               s->stream));
+    } else if (s->p.prec == LB_FP32) {
+        const StepArgs<float> a = make_args<float>(s);
+        LB_CUDA(s, delta_energy<float>(a.g_in, a.dpsi_in, s->p.nx, s->p.ny, a, s->res,
+                                       s->partials, s->counter, s->stream));
+    } else {
+        const StepArgs<__half> a = make_args<__half>(s);
+        LB_CUDA(s, delta_energy<__half>(a.g_in, a.dpsi_in, s->p.nx, s->p.ny, a, s->res,
+                                        s->partials, s->counter, s->stream));
+    }
+    double h[4];
+    LB_CUDA(s, cudaMemcpyAsync(h, s->res, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    LB_CUDA(s, cudaStreamSynchronize(s->stream));
+    for (int k = 0; k < 4; ++k) out[k] = h[k];
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(h[k])) return LB_ERR_NONFINITE;
+    return LB_OK;
+}
+
+lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy)
+{
+    if (!s) return LB_ERR_ARG;
+    if (s->poisoned) return LB_ERR_STATE;
+    LB_CUDA(s, cudaSetDevice(s->p.device));
+    const long long N = s->N;
+    double* outs[3] = {rho, ux, uy};
+    for (int k = 0; k < 3; ++k) {
+        if (!outs[k]) continue;
+        const bool dev = is_device_ptr(outs[k]);
+        double* dst = outs[k];
+        if (!dev) {
+            if (!s->field_tmp) {
+                if (cudaMalloc((void**)&s->field_tmp, sizeof(double) * N) != cudaSuccess) {
+                    cudaGetLastError();
+                    s->field_tmp = nullptr;
+                    return LB_ERR_OOM;
+                }
+            }
+            dst = s->field_tmp;
+        }
+        double* r = k == 0 ? dst : nullptr;
+        double* x = k == 1 ? dst : nullptr;
+        double* y = k == 2 ? dst : nullptr;
+        cudaError_t e;
+        if (s->p.prec == LB_FP64)
+            e = fp64_fields(s->f64[s->cur], s->p.nx, s->p.ny, r, x, y, s->stream);
+        else if (s->p.prec == LB_FP32)
+            e = delta_fields<float>(static_cast<const float*>(s->g[s->cur]), s->p.nx, s->p.ny,
+                                    s->rho_ref, r, x, y, s->stream);
+        else
+            e = delta_fields<__half>(static_cast<const __half*>(s->g[s->cur]), s->p.nx, s->p.ny,
+                                     s->rho_ref, r, x, y, s->stream);
+        if (e != cudaSuccess) return fail_cuda(s);
+        if (!dev)
+            LB_CUDA(s, cudaMemcpyAsync(outs[k], dst, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                                       s->stream));
+    }
+    LB_CUDA(s, cudaStreamSynchronize(s->stream));
+    return LB_OK;
+}
+
+lb_status lb_trace(lb_state* s, double* buf, int cap, int* count)
+{
+    if (!s || !count || cap < 0 || (cap > 0 && !buf)) return LB_ERR_ARG;
+    if (s->poisoned) return LB_ERR_STATE;
+    LB_CUDA(s, cudaSetDevice(s->p.device));
+    int total = 0;
+    LB_CUDA(s, cudaMemcpyAsync(&total, s->trace_count, sizeof(int), cudaMemcpyDeviceToHost,
+                               s->stream));
+    LB_CUDA(s, cudaStreamSynchronize(s->stream));
+    const int stored = total < kTraceCap ? total : kTraceCap;
+    const int n = stored < cap ? stored : cap;
+    // rows total-n .. total-1, oldest first; row r lives in ring slot r % kTraceCap,
+    // so the rows form at most two contiguous runs of the ring
+    int done = 0;
+    while (done < n) {
+        const int slot = (total - n + done) % kTraceCap;
+        int run = kTraceCap - slot;
+        if (run > n - done) run = n - done;
+        LB_CUDA(s, cudaMemcpyAsync(buf + (size_t)done * kTraceCols,
+                                   s->trace + (size_t)slot * kTraceCols,
+                                   sizeof(double) * kTraceCols * run, cudaMemcpyDeviceToHost,
+                                   s->stream));
+        done += run;
+    }
+    LB_CUDA(s, cudaStreamSynchronize(s->stream));
+    *count = n;
+    return LB_OK;
+}
+
+lb_status lb_get_launch(const lb_state* s, int* block_x, int* rows_per_cta)
+{
+    if (!s || !block_x || !rows_per_cta) return LB_ERR_ARG;
+    if (s->p.prec == LB_FP64) return LB_ERR_STATE;
+    *block_x = s->launch.block_x;
+    *rows_per_cta = s->launch.rows;
+    return LB_OK;
+}
+
+lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta)
+{
+    if (!s) return LB_ERR_ARG;
+    if (s->p.prec == LB_FP64) return LB_ERR_STATE;
+    if (block_x != 64 && block_x != 96 && block_x != 128 && block_x != 192 && block_x != 256)
+        return LB_ERR_ARG;
+    if (rows_per_cta < 16 || rows_per_cta > 4096) return LB_ERR_ARG;
+    // the CTA-partial buffer was sized for the smallest CTAs (64 threads, 16 rows)
+    if ((size_t)fp32_grid_blocks(s->p.nx, s->p.ny, Fp32Launch{block_x, rows_per_cta}) >
+        s->partials_cap)
+        return LB_ERR_ARG;
+    s->launch = Fp32Launch{block_x, rows_per_cta};
+    return LB_OK;
+}
+
+long lb_time(const lb_state* s) { return s ? (long)s->t : -1; }
+
+void lb_destroy(lb_state* s) { free_state(s); }
+
+}  // extern "C"

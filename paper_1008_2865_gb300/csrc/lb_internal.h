@@ -1,0 +1,91 @@
+// lb_internal.h — declarations shared by the translation units of liblbsc.so
+// (state layout, launch helpers). Not installed; the public interface is
+// include/lb.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "lb.h"
+
+namespace lbsc {
+
+constexpr int kTraceCap = 65536;     // rows kept in the device trace ring
+constexpr int kTraceCols = 5;        // (t, mass, E_s, E_m, E_bulk)
+
+// Couplings of the 24 links grouped by |c|^2 (Eq. FORCE with Table 1):
+//   K1 = G1/9 + 4 G2/63, K2 = G1/36 + 4 G2/135, K4 = G2/180,
+//   K5 = 2 G2/945, K8 = G2/15120; K0 = G1 4/9 + G2 p_s0 is the rest coupling
+//   of the belt-1 energy (p_s0 = 247/420 from Eq. weights_1).
+struct Couplings {
+    double K0, K1, K2, K4, K5, K8;
+};
+Couplings couplings(double G1, double G2);
+
+// Arguments of the fused FP32 step (deviation storage, see lb.h LB_FP32).
+template <typename T>
+struct StepArgs {
+    const T* __restrict__ g_in;      // [9][ny][nx] post-collision deviations of state t-1
+    T* __restrict__ g_out;           // [9][ny][nx] post-collision deviations of state t
+    const float* __restrict__ dpsi_in;   // [ny][nx] psi(t) - psi_ref
+    float* __restrict__ dpsi_out;        // [ny][nx] psi(t+1) - psi_ref
+    int nx, ny;
+    int rows;                        // output rows per CTA
+    long long N;                     // nx*ny
+    float omega, omc, inv_omega;     // omega, 1-omega, 1/omega
+    float w0, w1, w2;                // D2Q9 weights
+    float K1, K2, K4, K5, K8;        // force couplings
+    float rho_ref, psi_ref, cpsi, inv_rho0;  // dpsi = cpsi * expm1(-(rho-rho_ref)/rho0)
+    // energy/mass reduction (REDUCE launches only)
+    float K0, half_A1;
+    double* partials;                // [gridDim.x*gridDim.y][4]
+    unsigned int* counter;           // arrival counter for the last-block reduction
+    double* trace;                   // [kTraceCap][5] ring
+    int* trace_count;                // rows ever written
+    long long t;                     // time level of the reduced state
+};
+
+// Launchers (lb_fp32.cu). All return the launch's cudaError_t.
+struct Fp32Launch {
+    int block_x;   // threads per CTA = columns per CTA including the 2 halo columns
+    int rows;      // output rows per CTA
+};
+int fp32_grid_blocks(int nx, int ny, Fp32Launch L);
+cudaError_t fp32_step(const StepArgs<float>& a, Fp32Launch L, bool reduce, cudaStream_t s);
+cudaError_t fp16_step(const StepArgs<__half>& a, Fp32Launch L, bool reduce, cudaStream_t s);
+template <typename T>
+cudaError_t delta_init(T* g, float* dpsi, const double* rho_init, int nx, int ny,
+                       double rho_ref, double rho0, cudaStream_t s);
+template <typename T>
+cudaError_t delta_fields(const T* g, int nx, int ny, double rho_ref, double* rho, double* ux,
+                         double* uy, cudaStream_t s);
+template <typename T>
+cudaError_t delta_energy(const T* g, const float* dpsi, int nx, int ny, const StepArgs<T>& a,
+                         double* out4, double* partials, unsigned int* counter, cudaStream_t s);
+
+// Input checks and sums (lb_fp32.cu): out[0] = sum rho, flag |= 1 if any rho is
+// not finite or <= 0.
+cudaError_t rho_check_sum(const double* rho, long long n, double* partials, unsigned int* counter,
+                          double* out_sum, int* flag, cudaStream_t s);
+
+// FP64 parity path (lb_fp64.cu, compiled without FMA contraction).
+struct Fp64Args {
+    double* f_in;        // [9][ny][nx] populations of state t (after streaming)
+    double* f_out;       // [9][ny][nx] populations of state t+1
+    double* psi;         // [ny][nx] psi(t)
+    double* rho;         // [ny][nx] rho(t)
+    int nx, ny;
+    double omega, G1, G2, rho0;
+};
+cudaError_t fp64_init(double* f, const double* rho_init, int nx, int ny, cudaStream_t s);
+cudaError_t fp64_psi(const Fp64Args& a, cudaStream_t s);
+cudaError_t fp64_collide_stream(const Fp64Args& a, cudaStream_t s);
+cudaError_t fp64_energy(const Fp64Args& a, double* partials, unsigned int* counter,
+                        double* out4, double* trace, int* trace_count, long long t,
+                        cudaStream_t s);
+cudaError_t fp64_fields(const double* f, int nx, int ny, double* rho, double* ux, double* uy,
+                        cudaStream_t s);
+cudaError_t fp64_exp_cr(const double* x, double* y, long long n, cudaStream_t s);
+
+}  // namespace lbsc

@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (written here, from the targets the method is held to):
+  FP64 mode:  <= 1e-12 relative in rho and u over 1000 steps (the FP64 path
+              follows the oracle's operation order, so it is expected exact);
+  FP32 mode:  <= 1e-5 over 100 steps, measured as max|d rho| / max|rho| and
+              max|d u| / max|u| (u starts at 0, so pointwise relative error is
+              ill-posed); mass to 1e-6; pseudo-energy trace to 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1008_2865_gb300 import LBError, Lattice, capi, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _norm_err(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _run_gpu(rho0, steps, prec="fp32", launch=None, **kw):
+    with Lattice(rho0, prec=prec, **kw) as lat:
+        if launch:
+            lat.set_launch(*launch)
+        lat.step(steps)
+        rho, ux, uy = lat.fields()
+        tr = lat.trace()
+        en = lat.energy()
+        assert lat.t == steps
+    return rho, ux, uy, tr, en
+
+
+# ----------------------------------------------------------------- FP64 parity
+@pytest.mark.parametrize("G2", [0.0, 0.5])
+def test_fp64_1000_steps_128(G2):
+    """128x128, omega = 1, G1 = -5, rho = 0.7 + U(-0.01, 0.01), 1000 steps, trace every 10."""
+    rho0 = inputs.noisy_density(128, 128, seed=1, mean=0.7, amp=0.01, mode="abs")
+    ref = oracle.run(rho0, 1000, G1=-5.0, G2=G2, trace_every=10)
+    rho, ux, uy, tr, en = _run_gpu(rho0, 1000, prec="fp64", G1=-5.0, G2=G2, trace_every=10)
+    assert _norm_err(rho, ref[0]) <= 1e-12
+    assert _norm_err(ux, ref[1]) <= 1e-12 and _norm_err(uy, ref[2]) <= 1e-12
+    assert tr.shape == ref[3].shape == (100, 5)
+    assert np.array_equal(tr[:, 0], ref[3][:, 0])
+    assert np.max(np.abs(tr[:, 1:] - ref[3][:, 1:]) / np.abs(ref[3][:, 1:])) <= 1e-12
+    # phase separation happened: this is not a near-uniform comparison
+    assert rho.max() > 1.5 and rho.min() < 0.3
+
+
+def test_fp64_is_bit_exact_over_short_runs():
+    """Same operation order and a correctly rounded exp: identical bits."""
+    rho0 = inputs.noisy_density(37, 29, seed=2, mean=0.7, amp=0.05)
+    for G2, omega in [(0.0, 1.0), (0.7, 1.3)]:
+        ref = oracle.run(rho0, 25, omega=omega, G1=-5.0, G2=G2)
+        rho, ux, uy, _, _ = _run_gpu(rho0, 25, prec="fp64", omega=omega, G1=-5.0, G2=G2)
+        assert np.array_equal(rho, ref[0]) and np.array_equal(ux, ref[1])
+        assert np.array_equal(uy, ref[2])
+
+
+# ----------------------------------------------------------------- FP32 parity
+FP32_CASES = [
+    # (nx, ny, G2, omega, noise mode, seed)
+    (128, 128, 0.0, 1.0, "abs", 1),
+    (128, 128, 0.5, 1.0, "abs", 1),
+    (300, 200, 0.6, 1.0, "rel", 2),     # 3 ragged strips, ragged last row chunk
+    (131, 67, 0.9, 1.0, "rel", 3),
+    (256, 256, 0.3, 1.3, "rel", 4),     # omega != 1 exercises (1 - omega) f
+    (5, 5, 0.5, 1.0, "abs", 5),         # smallest lattice the stencil allows
+    (6, 7, 0.0, 0.9, "abs", 6),
+    (1024, 40, 0.6, 1.0, "rel", 8),     # many strips, one short chunk
+]
+
+
+@pytest.mark.parametrize("nx,ny,G2,omega,mode,seed", FP32_CASES)
+def test_fp32_100_steps(nx, ny, G2, omega, mode, seed):
+    rho0 = inputs.noisy_density(nx, ny, seed=seed, mean=0.7, amp=0.01, mode=mode)
+    ref = oracle.run(rho0, 100, omega=omega, G1=-5.0, G2=G2, trace_every=10)
+    rho, ux, uy, tr, en = _run_gpu(rho0, 100, omega=omega, G1=-5.0, G2=G2, trace_every=10)
+    assert _norm_err(rho, ref[0]) <= 1e-5
+    assert _norm_err(ux, ref[1]) <= 1e-5 and _norm_err(uy, ref[2]) <= 1e-5
+    assert np.array_equal(tr[:, 0], ref[3][:, 0])
+    assert np.max(np.abs(tr[:, 1] - ref[3][:, 1]) / ref[3][:, 1]) <= 1e-6          # mass
+    assert np.max(np.abs(tr[:, 2:] - ref[3][:, 2:]) / np.abs(ref[3][:, 2:])) <= 1e-4
+
+
+@pytest.mark.parametrize("launch", [(64, 16), (96, 17), (128, 16), (192, 40), (256, 33)])
+def test_fp32_launch_shapes_agree(launch):
+    """Every CTA shape gives the same trajectory (tile edges, halo columns, ragged tails)."""
+    rho0 = inputs.noisy_density(301, 170, seed=9, mean=0.7, amp=0.01, mode="rel")
+    ref = oracle.run(rho0, 60, G1=-5.0, G2=0.6, trace_every=10)
+    rho, ux, uy, tr, _ = _run_gpu(rho0, 60, launch=launch, G1=-5.0, G2=0.6, trace_every=10)
+    assert _norm_err(rho, ref[0]) <= 1e-5
+    assert _norm_err(ux, ref[1]) <= 1e-5 and _norm_err(uy, ref[2]) <= 1e-5
+    assert np.max(np.abs(tr[:, 2:] - ref[3][:, 2:]) / np.abs(ref[3][:, 2:])) <= 1e-4
+
+
+def test_fp32_energy_entry_matches_oracle_energy():
+    rho0 = inputs.noisy_density(90, 77, seed=10, mean=0.7, amp=0.01, mode="rel")
+    with Lattice(rho0, G1=-5.0, G2=0.6) as lat:
+        lat.step(40)
+        es, em, eb, mass = lat.energy()
+        rho, _, _ = lat.fields()
+    ref = oracle.run(rho0, 40, G1=-5.0, G2=0.6)
+    ps = oracle.psi(ref[0])
+    res, rem, reb = oracle.energy(ps, -5.0, 0.6)
+    assert abs(es - res) <= 1e-4 * abs(res) and abs(em - rem) <= 1e-4 * abs(rem)
+    assert abs(eb - reb) <= 1e-4 * abs(reb)
+    assert abs(mass - rho0.sum()) <= 1e-6 * rho0.sum()
+
+
+def test_fp32_is_deterministic():
+    rho0 = inputs.noisy_density(200, 150, seed=11, mean=0.7, amp=0.01, mode="rel")
+    a = _run_gpu(rho0, 50, G1=-5.0, G2=0.6, trace_every=5)
+    b = _run_gpu(rho0, 50, G1=-5.0, G2=0.6, trace_every=5)
+    for u, v in zip(a[:4], b[:4]):
+        assert np.array_equal(u, v)
+
+
+# ----------------------------------------------------------------- long-run observables
+def test_fp32_flat_interface_coexistence_densities():
+    """Coexistence densities of a flat interface agree with the oracle to 1e-3."""
+    nx, ny = 64, 5
+    x = np.arange(nx) + 0.5
+    prof = 0.156 + (1.93 - 0.156) * 0.5 * (np.tanh((x - 16) / 3) - np.tanh((x - 48) / 3))
+    rho0 = prof[None, :].repeat(ny, 0)
+    ref = oracle.run(rho0, 20000, G1=-5.0, G2=0.0)
+    rho, _, _, _, _ = _run_gpu(rho0, 20000, G1=-5.0, G2=0.0, trace_every=0)
+    for xs in (0, 32):
+        assert abs(rho[2, xs] - ref[0][2, xs]) <= 1e-3 * ref[0][2, xs]
+
+
+def test_fp32_mass_and_energy_trace_2000_steps():
+    rho0 = inputs.noisy_density(256, 256, seed=12, mean=0.7, amp=0.01, mode="rel")
+    ref = oracle.run(rho0, 2000, G1=-5.0, G2=0.6, trace_every=10)
+    rho, ux, uy, tr, _ = _run_gpu(rho0, 2000, G1=-5.0, G2=0.6, trace_every=10)
+    assert np.max(np.abs(tr[:, 1] - ref[3][:, 1]) / ref[3][:, 1]) <= 1e-6
+    # the trace stays within 1e-4 while the two trajectories are still close
+    early = tr[:, 0] <= 300
+    assert np.max(np.abs(tr[early, 2:] - ref[3][early, 2:]) / np.abs(ref[3][early, 2:])) <= 1e-4
+
+
+# ----------------------------------------------------------------- full size, sampled
+def test_fp32_full_size_8192_sampled():
+    """The 8192^2 roofline workload in the bench's launch shape, 3 steps: sampled sites
+    against the oracle run on a periodic 19x19 patch around each site (the dependency
+    cone of 3 steps has radius 9, so the patch reproduces the full lattice there)."""
+    torch = pytest.importorskip("torch")
+    n, steps, R = 8192, 3, 9
+    rho0 = inputs.noisy_density(n, n, seed=7, mean=0.7, amp=0.01, mode="rel")
+    dev_rho = torch.from_numpy(rho0).cuda()
+    with Lattice(dev_rho, G1=-5.0, G2=0.6, trace_every=10) as lat:
+        lat.step(steps)
+        out = torch.empty((3, n, n), dtype=torch.float64, device="cuda")
+        lat.fields(out[0], out[1], out[2])
+        e = lat.energy()
+    fields = out.cpu().numpy()
+    del out, dev_rho
+    rng = np.random.default_rng(5)
+    ys = list(rng.integers(0, n, 40)) + [0, n - 1, 0, n - 1, 63, 64, 4095]
+    xs = list(rng.integers(0, n, 40)) + [0, n - 1, n - 1, 0, 125, 126, 127]
+    worst = [0.0, 0.0]
+    for y, x in zip(ys, xs):
+        yy = (np.arange(y - R, y + R + 1)) % n
+        xx = (np.arange(x - R, x + R + 1)) % n
+        patch = rho0[np.ix_(yy, xx)]
+        r, ux, uy, _ = oracle.run(patch, steps, G1=-5.0, G2=0.6)
+        worst[0] = max(worst[0], abs(fields[0, y, x] - r[R, R]))
+        worst[1] = max(worst[1], abs(fields[1, y, x] - ux[R, R]), abs(fields[2, y, x] - uy[R, R]))
+    assert worst[0] <= 1e-5 * 0.71
+    assert worst[1] <= 1e-5 * max(np.max(np.abs(fields[1])), 1e-12)
+    assert abs(e[3] - rho0.sum()) <= 1e-6 * rho0.sum()
+
+
+# ----------------------------------------------------------------- edge cases
+def test_invalid_density_rejected():
+    for bad in (np.nan, 0.0, -0.1, np.inf):
+        rho0 = np.full((8, 8), 0.7)
+        rho0[3, 4] = bad
+        with pytest.raises(LBError) as ei:
+            Lattice(rho0)
+        assert ei.value.status == capi.LB_ERR_ARG
+
+
+def test_step_arguments_and_time():
+    rho0 = inputs.noisy_density(16, 16, seed=1)
+    with Lattice(rho0) as lat:
+        assert lat.t == 0
+        lat.step(0)
+        assert lat.t == 0
+        with pytest.raises(LBError):
+            capi.lb_step(lat.handle, -1)
+        lat.step(7)
+        assert lat.t == 7
+        with pytest.raises(LBError):
+            lat.set_launch(100, 16)
+        with pytest.raises(LBError):
+            lat.set_launch(128, 8)
+
+
+def test_device_pointers_and_partial_fields():
+    torch = pytest.importorskip("torch")
+    rho0 = inputs.noisy_density(40, 30, seed=3)
+    with Lattice(torch.from_numpy(rho0).cuda(), G2=0.5) as lat:
+        lat.step(20)
+        r = torch.empty((30, 40), dtype=torch.float64, device="cuda")
+        lat.fields(rho=r)
+        h_rho, h_ux, _ = lat.fields()
+        assert np.array_equal(r.cpu().numpy(), h_rho)
+        only_ux = np.empty((30, 40))
+        lat.fields(ux=only_ux)
+        assert np.array_equal(only_ux, h_ux)
+
+
+def test_trace_rows_and_ring():
+    rho0 = inputs.noisy_density(24, 24, seed=4)
+    with Lattice(rho0, trace_every=3) as lat:
+        lat.step(10)
+        tr = lat.trace()
+        assert list(tr[:, 0]) == [0, 3, 6, 9]
+        assert len(lat.trace(cap=2)) == 2 and list(lat.trace(cap=2)[:, 0]) == [6, 9]
+    with Lattice(rho0, trace_every=0) as lat:
+        lat.step(10)
+        assert len(lat.trace()) == 0
+
+
+def test_fp64_energy_matches_oracle():
+    rho0 = inputs.noisy_density(33, 35, seed=6, amp=0.05)
+    with Lattice(rho0, prec="fp64", G2=0.8) as lat:
+        lat.step(30)
+        es, em, eb, mass = lat.energy()
+    ref = oracle.run(rho0, 30, G1=-5.0, G2=0.8)
+    r = oracle.energy(oracle.psi(ref[0]), -5.0, 0.8)
+    assert np.allclose([es, em, eb], r, rtol=1e-13, atol=0)
+    assert abs(mass - ref[0].sum()) <= 1e-13 * mass
