@@ -36,7 +36,7 @@ G1, G2, OMEGA, SEED = -5.0, 0.6, 1.0, 7
 TRACE_EVERY = 10
 BYTES_PER_SITE = 80          # 36 B g* in + 36 B g* out + 4 B dpsi in + 4 B dpsi out
 METRIC = "MLUPS and % HBM roofline (FP32 fused step, 1 GB300); adjoint+batched vs plain"
-WORKLOAD = ("8192x8192 periodic D2Q9 two-belt Shan-Chen, FP32 (deviation storage), omega=1, "
+WORKLOAD = ("{n}x{n} periodic D2Q9 two-belt Shan-Chen, FP32 (deviation storage), omega=1, "
             "G1=-5.0, G2=0.6, rho=0.7(1+-1%) seeded uniform noise (seed 7), energy+mass "
             "reduction every 10 steps")
 
@@ -58,7 +58,7 @@ def _peaks():
         return 6800.0, "fallback (6.8 TB/s, earlier GB300 copy measurement)"
 
 
-def _traffic_record(kernel_file):
+def _traffic_record(kernel_file, nx, ny):
     """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
     rec_path = os.path.join(ROOT, "profiles", "step_fp32_traffic.json")
     try:
@@ -66,7 +66,7 @@ def _traffic_record(kernel_file):
             rec = json.load(fh)
         with open(kernel_file, "rb") as fh:
             sha = hashlib.sha256(fh.read()).hexdigest()
-        if rec.get("source_sha256") == sha and rec.get("nx") == NX and rec.get("ny") == NY:
+        if rec.get("source_sha256") == sha and rec.get("nx") == nx and rec.get("ny") == ny:
             return float(rec["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -160,7 +160,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 noise)", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": f"{n}x{n} periodic lattice per step"},
+            "config": {"workload": WORKLOAD.format(n=NX), "sample": f"{n}x{n} periodic lattice per step"},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.threads(),
                              "kind": "oracle",
                              "sample": f"each step one full step of a {n}x{n} lattice"},
@@ -184,6 +184,7 @@ def run_ours(args):
     capi.load(build_if_missing=True)
     stream = torch.cuda.current_stream()
 
+    NX = NY = args.size
     rho0 = inputs.noisy_density(NX, NY, SEED + rank, mean=0.7, amp=0.01, mode="rel")
 
     def barrier():
@@ -201,8 +202,15 @@ def run_ours(args):
         return float(t.item())
 
     # ---- device-resident timing: inputs already in HBM
-    lat = Lattice(rho0, omega=OMEGA, G1=G1, G2=G2, prec="fp32", trace_every=TRACE_EVERY,
+    lat = Lattice(rho0, omega=OMEGA, G1=G1, G2=G2, prec=args.prec, trace_every=TRACE_EVERY,
                   device=dev, stream=stream.cuda_stream)
+    if args.launch:
+        lat.set_launch(*(int(v) for v in args.launch.split(",")))
+    elif args.prec != "fp64":
+        from paper_1008_2865_gb300 import tune
+        best = tune.lookup(NX, NY, args.prec)
+        if best and len(best) == 3:
+            lat.set_launch(*best)
     lat.step(args.warmup)
     # align the timed region to a trace period so it holds K/10 reduction steps
     lat.step((-lat.t) % TRACE_EVERY)
@@ -230,16 +238,25 @@ def run_ours(args):
     value = N * args.steps * ws / (ms_max / 1e3) / 1e6
     per_launch_s = ms / 1e3 / args.steps
     peak, peak_src = _peaks()
-    achieved = BYTES_PER_SITE * N / per_launch_s / 1e9
-    traffic = _traffic_record(os.path.join(ROOT, "paper_1008_2865_gb300", "csrc", "lb_fp32.cu"))
+    achieved = (BYTES_PER_SITE if args.prec == "fp32" else 44) * N / per_launch_s / 1e9
+    traffic = _traffic_record(os.path.join(ROOT, "paper_1008_2865_gb300", "csrc", "lb_fp32.cu"),
+                              NX, NY)
+    bytes_per_site = BYTES_PER_SITE if args.prec == "fp32" else 44
+
+    if args.skip_e2e:
+        print(json.dumps({"size": NX, "prec": args.prec, "launch": launch, "MLUPS": value,
+                          "ms_per_step": ms / args.steps,
+                          "GBs": bytes_per_site * N / per_launch_s / 1e9}))
+        return 0
 
     # ---- end to end through the public API with host buffers
     pinned_in = torch.from_numpy(rho0).pin_memory()
     pinned_out = torch.empty((NY, NX), dtype=torch.float64).pin_memory()
     barrier()
     t0 = time.perf_counter()
-    lat2 = Lattice(pinned_in, omega=OMEGA, G1=G1, G2=G2, prec="fp32", trace_every=TRACE_EVERY,
-                   device=dev, stream=stream.cuda_stream)
+    lat2 = Lattice(pinned_in, omega=OMEGA, G1=G1, G2=G2, prec=args.prec,
+                   trace_every=TRACE_EVERY, device=dev, stream=stream.cuda_stream)
+    lat2.set_launch(*launch)
     rows_read = 0
     for k in range(args.steps):
         lat2.step(1)
@@ -258,17 +275,20 @@ def run_ours(args):
         out = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.prec == "fp32" else "f32 (f16 storage)",
             "data": "synthetic (seeded SplitMix64 noise)",
-            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY,
+            "config": {"workload": WORKLOAD.format(n=NX), "nx": NX, "ny": NY,
                        "l2": "state 5.4 GB per replica >> 129 MB L2; no flush needed",
-                       "launch": {"block_x": launch[0], "rows_per_cta": launch[1]},
+                       "launch": {"block_x": launch[0], "rows_per_cta": launch[1],
+                                  "pipeline": ["register-prefetch", "bulk-copy rings"][launch[2]]},
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
-                         "kernel": "k_step<float,128,*> (one launch per step)",
-                         "bytes_per_site": BYTES_PER_SITE},
+                         "kernel": ("k_step_bulk" if launch[2] else "k_step")
+                                   + " (one launch per step)",
+                         "bytes_per_site": bytes_per_site},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "MLUPS",
                     "h2d_bytes_per_step": 8 * N / args.steps,
@@ -293,6 +313,12 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=8192,
+                    help="lattice side (profiling of smaller cases; the benchmark is 8192)")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16_delta"])
+    ap.add_argument("--launch", default=None, help="block_x,rows_per_cta,pipeline override")
+    ap.add_argument("--skip-e2e", action="store_true",
+                    help="time the device-resident steps only and print a short line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -39,7 +39,8 @@ typedef enum {
     LB_ERR_CUDA = -2,       /* a CUDA call failed; the state is poisoned */
     LB_ERR_OOM = -3,        /* device allocation failed; nothing was created */
     LB_ERR_NONFINITE = -4,  /* the lattice holds a NaN/Inf density or energy */
-    LB_ERR_STATE = -5       /* call not valid in the state's current condition */
+    LB_ERR_STATE = -5,      /* call not valid in the state's current condition */
+    LB_ERR_TIMEOUT = -6     /* a bounded in-kernel wait ran out; the state is poisoned */
 } lb_status;
 
 /* Pseudopotential form. Sec. 2: psi = sqrt(rho0) (1 - exp(-rho/rho0)),
@@ -115,15 +116,33 @@ lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy);
  * Errors: LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA. */
 lb_status lb_trace(lb_state* s, double* buf, int cap, int* count);
 
-/* Launch shape of the fused FP32/FP16 step kernel: CTAs of block_x threads
- * cover block_x - 2 output columns (one halo column each side) and
- * rows_per_cta output rows. lb_set_launch accepts block_x in
- * {64, 96, 128, 192, 256} and rows_per_cta in [16, 4096]; it changes only how
- * the work is split, not the result beyond FP32 rounding of the energy
- * partial sums. Both return LB_ERR_ARG for NULL or out-of-range arguments and
- * LB_ERR_STATE for an FP64 state (whose kernels have no such shape). */
-lb_status lb_get_launch(const lb_state* s, int* block_x, int* rows_per_cta);
-lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta);
+/* Launch shape of the fused FP32/FP16 step kernel. A CTA of block_x threads
+ * marches over rows_per_cta output rows of a strip of columns, one thread per
+ * column plus a one-column halo on each side. pipeline selects how the input
+ * rows reach the CTA:
+ *   0  register prefetch: each thread loads its populations of the next row
+ *      from global memory (any lattice shape; block_x in {64, 96, 128, 192, 256},
+ *      block_x - 2 output columns per CTA);
+ *   1  bulk-copy rings: the bulk-copy (TMA) engine stages whole rows in shared
+ *      memory several rows ahead (block_x in {64, 128, 256}; needs nx a
+ *      multiple of 16 bytes' worth of elements and nx >= block_x + 8).
+ * lb_init picks pipeline 1 where the shape allows it. rows_per_cta is in
+ * [16, 4096]. The shape changes how the work is split, not the trajectory;
+ * only the FP32 rounding of the energy partial sums depends on it.
+ * Errors: LB_ERR_ARG for NULL or unsupported values, LB_ERR_STATE for an FP64
+ * state (whose kernels have no such shape). */
+lb_status lb_get_launch(const lb_state* s, int* block_x, int* rows_per_cta, int* pipeline);
+lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta, int pipeline);
+
+/* Bound on every in-kernel wait of the bulk-copy pipeline, in SM clock cycles
+ * (default 2e9, about one second at GB300 clocks). A wait that runs out makes
+ * the kernel record an error and return; the next synchronising call
+ * (lb_energy, lb_fields, lb_trace) reports LB_ERR_TIMEOUT and poisons the
+ * state, while the CUDA context stays usable. extra_expect_bytes is a test
+ * hook: when nonzero every row's barrier expects that many bytes more than
+ * its copies deliver, so the waits run out on purpose; use 0 otherwise.
+ * Errors: LB_ERR_ARG (NULL, cycles <= 0). */
+lb_status lb_set_wait_limit(lb_state* s, long long cycles, unsigned int extra_expect_bytes);
 
 /* Current time step t (number of lb_step steps taken since lb_init); -1 for NULL. */
 long lb_time(const lb_state* s);

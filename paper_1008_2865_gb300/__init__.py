@@ -11,8 +11,8 @@ import numpy as np
 
 from . import capi, inputs  # noqa: F401
 from .capi import (LBError, lb_destroy, lb_energy, lb_fields, lb_get_launch,  # noqa: F401
-                   lb_init, lb_set_launch, lb_status_str, lb_step, lb_time, lb_trace,
-                   make_params)
+                   lb_init, lb_set_launch, lb_set_wait_limit, lb_status_str, lb_step, lb_time,
+                   lb_trace, make_params)
 
 
 def couplings_from_A(A1: float, A2: float, lam: float = 1.5):
@@ -58,11 +58,13 @@ class Lattice:
 
     @property
     def launch(self):
-        """(block_x, rows_per_cta) of the fused step kernel."""
+        """(block_x, rows_per_cta, pipeline) of the fused step kernel."""
         return lb_get_launch(self.handle)
 
-    def set_launch(self, block_x: int, rows_per_cta: int) -> None:
-        lb_set_launch(self.handle, block_x, rows_per_cta)
+    def set_launch(self, block_x: int, rows_per_cta: int, pipeline: int = None) -> None:
+        if pipeline is None:
+            pipeline = self.launch[2]
+        lb_set_launch(self.handle, block_x, rows_per_cta, pipeline)
 
     def trace(self, cap: int = 65536):
         return lb_trace(self.handle, cap)

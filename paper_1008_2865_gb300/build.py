@@ -23,6 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {
     "lb_api.cu": [],
     "lb_fp32.cu": [],
+    "lb_bulk.cu": [],
     "lb_fp64.cu": ["--fmad=false"],
 }
 
@@ -49,7 +50,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if needed) and return the path of liblbsc.so."""
     os.makedirs(LIBDIR, exist_ok=True)
     os.makedirs(BUILDDIR, exist_ok=True)
-    headers = [os.path.join(CSRC, "lb_internal.h"), os.path.join(INCLUDE, "lb.h")]
+    headers = [os.path.join(CSRC, "lb_internal.h"), os.path.join(CSRC, "lb_device.cuh"),
+               os.path.join(INCLUDE, "lb.h")]
     nvcc = _nvcc()
     objs = []
     jobs = []

@@ -19,6 +19,7 @@ import numpy as np
 from . import build as _build
 
 LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_OOM, LB_ERR_NONFINITE, LB_ERR_STATE = 0, -1, -2, -3, -4, -5
+LB_ERR_TIMEOUT = -6
 LB_PSI_SC_EXP = 0
 LB_FP32, LB_FP64, LB_FP16_DELTA = 0, 1, 2
 
@@ -76,10 +77,12 @@ def load(build_if_missing: bool = False):
             lib.lb_time.argtypes = [vp]
             lib.lb_time.restype = ctypes.c_long
             ip = ctypes.POINTER(ctypes.c_int)
-            lib.lb_get_launch.argtypes = [vp, ip, ip]
+            lib.lb_get_launch.argtypes = [vp, ip, ip, ip]
             lib.lb_get_launch.restype = ctypes.c_int
-            lib.lb_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            lib.lb_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.lb_set_launch.restype = ctypes.c_int
+            lib.lb_set_wait_limit.argtypes = [vp, ctypes.c_longlong, ctypes.c_uint]
+            lib.lb_set_wait_limit.restype = ctypes.c_int
             lib.lb_destroy.argtypes = [vp]
             lib.lb_destroy.restype = None
             lib.lb_status_str.argtypes = [ctypes.c_int]
@@ -158,16 +161,21 @@ def lb_trace(h: int, cap: int = 65536) -> np.ndarray:
 
 
 def lb_get_launch(h: int):
-    """(block_x, rows_per_cta) of the fused step kernel."""
-    bx, rows = ctypes.c_int(0), ctypes.c_int(0)
-    _check(load().lb_get_launch(ctypes.c_void_p(h), ctypes.byref(bx), ctypes.byref(rows)),
-           "lb_get_launch")
-    return bx.value, rows.value
+    """(block_x, rows_per_cta, pipeline) of the fused step kernel."""
+    bx, rows, pipe = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().lb_get_launch(ctypes.c_void_p(h), ctypes.byref(bx), ctypes.byref(rows),
+                                ctypes.byref(pipe)), "lb_get_launch")
+    return bx.value, rows.value, pipe.value
 
 
-def lb_set_launch(h: int, block_x: int, rows_per_cta: int) -> None:
-    _check(load().lb_set_launch(ctypes.c_void_p(h), int(block_x), int(rows_per_cta)),
-           "lb_set_launch")
+def lb_set_launch(h: int, block_x: int, rows_per_cta: int, pipeline: int) -> None:
+    _check(load().lb_set_launch(ctypes.c_void_p(h), int(block_x), int(rows_per_cta),
+                                int(pipeline)), "lb_set_launch")
+
+
+def lb_set_wait_limit(h: int, cycles: int, extra_expect_bytes: int = 0) -> None:
+    _check(load().lb_set_wait_limit(ctypes.c_void_p(h), int(cycles), int(extra_expect_bytes)),
+           "lb_set_wait_limit")
 
 
 def lb_time(h) -> int:

@@ -41,7 +41,10 @@ struct lb_state {
     float* dpsi[2] = {nullptr, nullptr};
     int cur = 0;
     double rho_ref = 0.0;
-    Fp32Launch launch{128, 64};
+    Fp32Launch launch{128, 64, 0};
+    int* err = nullptr;            // set by a kernel whose bounded wait ran out
+    long long wait_cycles = 2000000000LL;
+    unsigned int extra_tx = 0;
     // FP64 parity storage
     double* f64[2] = {nullptr, nullptr};
     double* psi64 = nullptr;
@@ -86,13 +89,19 @@ lb_status validate(const lb_params* p)
     return LB_OK;
 }
 
-// Default launch shape: 128-thread strips, rows chosen for about four waves
-// of 8 resident CTAs per SM on a 152-SM part, at least 16 rows.
-Fp32Launch default_launch(int nx, int ny)
+size_t elem_size(lb_precision p) { return p == LB_FP16_DELTA ? 2 : 4; }
+
+// Default launch shape: 128-thread strips, the bulk-copy pipeline where the
+// shape allows it, rows chosen for about four waves of the resident CTAs on a
+// 152-SM part (5 per SM with the rings, 8 without), at least 16 rows.
+Fp32Launch default_launch(int nx, int ny, lb_precision prec)
 {
-    Fp32Launch L{128, 64};
-    const long long strips = (nx + L.block_x - 3) / (L.block_x - 2);
-    const long long target = 152LL * 8 * 4;
+    Fp32Launch L{128, 64, 0};
+    const int es = (int)elem_size(prec);
+    if (bulk_supported(nx, ny, es, 128)) L.pipeline = 1;
+    const int per = L.pipeline ? (es == 2 ? 120 : 124) : 126;
+    const long long strips = (nx + per - 1) / per;
+    const long long target = 152LL * (L.pipeline ? 5 : 8) * 4;
     long long rows = (strips * ny + target - 1) / target;
     if (rows < 16) rows = 16;
     if (rows > 512) rows = 512;
@@ -100,7 +109,13 @@ Fp32Launch default_launch(int nx, int ny)
     return L;
 }
 
-size_t elem_size(lb_precision p) { return p == LB_FP16_DELTA ? 2 : 4; }
+// CTA count of a launch shape (the CTA-partial buffer is sized for the largest)
+size_t step_blocks(const lb_state* s, Fp32Launch L)
+{
+    if (L.pipeline == 1)
+        return (size_t)bulk_grid_blocks(s->p.nx, s->p.ny, (int)elem_size(s->p.prec), L);
+    return (size_t)fp32_grid_blocks(s->p.nx, s->p.ny, L);
+}
 
 template <typename T>
 StepArgs<T> make_args(const lb_state* s)
@@ -138,6 +153,9 @@ StepArgs<T> make_args(const lb_state* s)
     a.trace = s->trace;
     a.trace_count = s->trace_count;
     a.t = s->t;
+    a.err = s->err;
+    a.wait_cycles = s->wait_cycles;
+    a.extra_tx = s->extra_tx;
     return a;
 }
 
@@ -146,6 +164,21 @@ lb_status fail_cuda(lb_state* s)
     if (s) s->poisoned = true;
     cudaGetLastError();
     return LB_ERR_CUDA;
+}
+
+// Read the kernels' wait-timeout flag (synchronises the stream).
+lb_status check_err(lb_state* s)
+{
+    int e = 0;
+    if (cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return fail_cuda(s);
+    if (e) {
+        s->poisoned = true;
+        return LB_ERR_TIMEOUT;
+    }
+    return LB_OK;
 }
 
 #define LB_CUDA(s, call)                          \
@@ -160,7 +193,7 @@ void free_state(lb_state* s)
     cudaStreamSynchronize(s->stream);
     void* ptrs[] = {s->g[0], s->g[1], s->dpsi[0], s->dpsi[1], s->f64[0], s->f64[1], s->psi64,
                     s->rho64, s->partials, s->counter, s->trace, s->trace_count, s->res,
-                    s->flag, s->field_tmp};
+                    s->flag, s->field_tmp, s->err};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     cudaGetLastError();
@@ -172,10 +205,13 @@ lb_status step_fp32(lb_state* s, long n)
     for (long k = 0; k < n; ++k) {
         const bool reduce = s->p.trace_every > 0 && (s->t % s->p.trace_every) == 0;
         cudaError_t e;
+        const bool bulk = s->launch.pipeline == 1;
         if (s->p.prec == LB_FP32)
-            e = fp32_step(make_args<float>(s), s->launch, reduce, s->stream);
+            e = bulk ? fp32_step_bulk(make_args<float>(s), s->launch, reduce, s->stream)
+                     : fp32_step(make_args<float>(s), s->launch, reduce, s->stream);
         else
-            e = fp16_step(make_args<__half>(s), s->launch, reduce, s->stream);
+            e = bulk ? fp16_step_bulk(make_args<__half>(s), s->launch, reduce, s->stream)
+                     : fp16_step(make_args<__half>(s), s->launch, reduce, s->stream);
         if (e != cudaSuccess) return fail_cuda(s);
         s->cur ^= 1;
         s->t += 1;
@@ -227,6 +263,7 @@ const char* lb_status_str(lb_status st)
     case LB_ERR_OOM: return "device allocation failed";
     case LB_ERR_NONFINITE: return "non-finite density or energy";
     case LB_ERR_STATE: return "call not valid in the current state";
+    case LB_ERR_TIMEOUT: return "an in-kernel wait ran out (state poisoned)";
     }
     return "unknown status";
 }
@@ -254,14 +291,18 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
         }
         return true;
     };
-    s->launch = default_launch(p->nx, p->ny);
-    const size_t nblk_step = (size_t)fp32_grid_blocks(p->nx, p->ny, Fp32Launch{64, 16});
+    s->launch = default_launch(p->nx, p->ny, p->prec);
+    size_t nblk_step = (size_t)fp32_grid_blocks(p->nx, p->ny, Fp32Launch{64, 16, 0});
+    const size_t nblk_bulk =
+        (size_t)bulk_grid_blocks(p->nx, p->ny, (int)elem_size(p->prec), Fp32Launch{64, 16, 1});
+    if (nblk_bulk > nblk_step) nblk_step = nblk_bulk;
     s->partials_cap = nblk_step > 152 * 16 ? nblk_step : 152 * 16;
     bool ok = alloc((void**)&s->partials, 4 * sizeof(double) * s->partials_cap) &&
               alloc((void**)&s->counter, sizeof(unsigned int)) &&
               alloc((void**)&s->trace, sizeof(double) * kTraceCap * kTraceCols) &&
               alloc((void**)&s->trace_count, sizeof(int)) &&
-              alloc((void**)&s->res, 4 * sizeof(double)) && alloc((void**)&s->flag, sizeof(int));
+              alloc((void**)&s->res, 4 * sizeof(double)) && alloc((void**)&s->flag, sizeof(int)) &&
+              alloc((void**)&s->err, sizeof(int));
     if (ok && p->prec == LB_FP64) {
         ok = alloc((void**)&s->f64[0], 9 * sizeof(double) * N) &&
              alloc((void**)&s->f64[1], 9 * sizeof(double) * N) &&
@@ -295,7 +336,8 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
                         s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->counter, 0, sizeof(unsigned int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->trace_count, 0, sizeof(int), s->stream) != cudaSuccess ||
-        cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream) != cudaSuccess)
+        cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->err, 0, sizeof(int), s->stream) != cudaSuccess)
         return bail(LB_ERR_CUDA);
     if (rho_check_sum(rho_dev, N, s->partials, s->counter, s->res, s->flag, s->stream) !=
         cudaSuccess)
@@ -357,6 +399,10 @@ lb_status lb_energy(lb_state* s, double out[4])
     double h[4];
     LB_CUDA(s, cudaMemcpyAsync(h, s->res, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     LB_CUDA(s, cudaStreamSynchronize(s->stream));
+    {
+        const lb_status st = check_err(s);
+        if (st != LB_OK) return st;
+    }
     for (int k = 0; k < 4; ++k) out[k] = h[k];
     for (int k = 0; k < 4; ++k)
         if (!std::isfinite(h[k])) return LB_ERR_NONFINITE;
@@ -402,7 +448,7 @@ lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy)
                                        s->stream));
     }
     LB_CUDA(s, cudaStreamSynchronize(s->stream));
-    return LB_OK;
+    return check_err(s);
 }
 
 lb_status lb_trace(lb_state* s, double* buf, int cap, int* count)
@@ -431,30 +477,46 @@ lb_status lb_trace(lb_state* s, double* buf, int cap, int* count)
     }
     LB_CUDA(s, cudaStreamSynchronize(s->stream));
     *count = n;
-    return LB_OK;
+    return check_err(s);
 }
 
-lb_status lb_get_launch(const lb_state* s, int* block_x, int* rows_per_cta)
+lb_status lb_get_launch(const lb_state* s, int* block_x, int* rows_per_cta, int* pipeline)
 {
-    if (!s || !block_x || !rows_per_cta) return LB_ERR_ARG;
+    if (!s || !block_x || !rows_per_cta || !pipeline) return LB_ERR_ARG;
     if (s->p.prec == LB_FP64) return LB_ERR_STATE;
     *block_x = s->launch.block_x;
     *rows_per_cta = s->launch.rows;
+    *pipeline = s->launch.pipeline;
     return LB_OK;
 }
 
-lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta)
+lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta, int pipeline)
 {
     if (!s) return LB_ERR_ARG;
     if (s->p.prec == LB_FP64) return LB_ERR_STATE;
-    if (block_x != 64 && block_x != 96 && block_x != 128 && block_x != 192 && block_x != 256)
-        return LB_ERR_ARG;
     if (rows_per_cta < 16 || rows_per_cta > 4096) return LB_ERR_ARG;
-    // the CTA-partial buffer was sized for the smallest CTAs (64 threads, 16 rows)
-    if ((size_t)fp32_grid_blocks(s->p.nx, s->p.ny, Fp32Launch{block_x, rows_per_cta}) >
-        s->partials_cap)
+    if (pipeline == 0) {
+        if (block_x != 64 && block_x != 96 && block_x != 128 && block_x != 192 && block_x != 256)
+            return LB_ERR_ARG;
+    } else if (pipeline == 1) {
+        if (block_x != 64 && block_x != 128 && block_x != 256) return LB_ERR_ARG;
+        if (!bulk_supported(s->p.nx, s->p.ny, (int)elem_size(s->p.prec), block_x))
+            return LB_ERR_ARG;
+    } else {
         return LB_ERR_ARG;
-    s->launch = Fp32Launch{block_x, rows_per_cta};
+    }
+    const Fp32Launch L{block_x, rows_per_cta, pipeline};
+    // the CTA-partial buffer was sized for the smallest CTAs (64 threads, 16 rows)
+    if (step_blocks(s, L) > s->partials_cap) return LB_ERR_ARG;
+    s->launch = L;
+    return LB_OK;
+}
+
+lb_status lb_set_wait_limit(lb_state* s, long long cycles, unsigned int extra_expect_bytes)
+{
+    if (!s || cycles <= 0) return LB_ERR_ARG;
+    s->wait_cycles = cycles;
+    s->extra_tx = extra_expect_bytes;
     return LB_OK;
 }
 

@@ -1,0 +1,205 @@
+// lb_device.cuh — device helpers shared by the FP32/FP16 step kernels: the
+// per-site physics of one lattice Boltzmann step (Chibbaro et al.,
+// arXiv:1008.2865) and the deterministic CTA/grid reductions.
+#pragma once
+
+#include "lb_internal.h"
+
+namespace lbsc {
+namespace dev {
+
+__device__ __forceinline__ float ldg_(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg_(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ void st_(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ float lds_(const float* p) { return *p; }
+__device__ __forceinline__ float lds_(const __half* p) { return __half2float(*p); }
+
+__device__ __forceinline__ int wrapi(int a, int n)
+{
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+// Two-belt force sums of Eq. FORCE in pair form. r[k] points at the stencil
+// centre's column in the dpsi row y + k - 2 (k = 0..4), so r[k][dx] is
+// dpsi(x + dx, y + k - 2). Returns S = sum_c K_c c dpsi(x + c), grouped by
+// |c|^2; the constant psi_ref cancels inside every pair (c, -c).
+template <typename T>
+__device__ __forceinline__ void force_sums(const float* const r[5], const StepArgs<T>& a,
+                                           float& Sx, float& Sy)
+{
+    const float *rM2 = r[0], *rM1 = r[1], *rC = r[2], *rP1 = r[3], *rP2 = r[4];
+    const float d10 = rC[1] - rC[-1];
+    const float d01 = rP1[0] - rM1[0];
+    const float d11 = rP1[1] - rM1[-1];   // (1,1) - (-1,-1)
+    const float d1m = rM1[1] - rP1[-1];   // (1,-1) - (-1,1)
+    const float d20 = rC[2] - rC[-2];
+    const float d02 = rP2[0] - rM2[0];
+    const float da = rP1[2] - rM1[-2];    // (2,1) - (-2,-1)
+    const float db = rP2[1] - rM2[-1];    // (1,2) - (-1,-2)
+    const float dc = rP2[-1] - rM2[1];    // (-1,2) - (1,-2)
+    const float dd = rP1[-2] - rM1[2];    // (-2,1) - (2,-1)
+    const float e1 = rP2[2] - rM2[-2];    // (2,2) - (-2,-2)
+    const float e2 = rM2[2] - rP2[-2];    // (2,-2) - (-2,2)
+    Sx = a.K1 * d10 + a.K2 * (d11 + d1m) + 2.f * a.K4 * d20 +
+         a.K5 * (2.f * (da - dd) + (db - dc)) + 2.f * a.K8 * (e1 + e2);
+    Sy = a.K1 * d01 + a.K2 * (d11 - d1m) + 2.f * a.K4 * d02 +
+         a.K5 * ((da + dd) + 2.f * (db + dc)) + 2.f * a.K8 * (e1 - e2);
+}
+
+// Sec. 5 pseudo-energy densities of one site with psi = psi_ref + dpsi:
+// belt 1 with the rest coupling K0, belt 2, and the bulk term A1/2 psi^2.
+template <typename T>
+__device__ __forceinline__ void energy_site(const float* const r[5], float pc,
+                                            const StepArgs<T>& a, float& es, float& em,
+                                            float& eb)
+{
+    const float *rM2 = r[0], *rM1 = r[1], *rC = r[2], *rP1 = r[3], *rP2 = r[4];
+    const float pr = a.psi_ref;
+    const float S1 = (rC[1] + rC[-1]) + (rP1[0] + rM1[0]);
+    const float S2 = (rP1[1] + rP1[-1]) + (rM1[1] + rM1[-1]);
+    const float S4 = (rC[2] + rC[-2]) + (rP2[0] + rM2[0]);
+    const float S5 = ((rP1[2] + rP1[-2]) + (rM1[2] + rM1[-2])) +
+                     ((rP2[1] + rP2[-1]) + (rM2[1] + rM2[-1]));
+    const float S8 = (rP2[2] + rP2[-2]) + (rM2[2] + rM2[-2]);
+    const float b1 = a.K0 * pc + a.K1 * fmaf(4.f, pr, S1) + a.K2 * fmaf(4.f, pr, S2);
+    const float b2 = a.K4 * fmaf(4.f, pr, S4) + a.K5 * fmaf(8.f, pr, S5) + a.K8 * fmaf(4.f, pr, S8);
+    es = fmaf(0.5f * pc, b1, es);
+    em = fmaf(0.5f * pc, b2, em);
+    eb = fmaf(a.half_A1 * pc, pc, eb);
+}
+
+// Moments (Eqs. 2-3) and BGK relaxation (Eq. 1) of the pulled deviations
+// f_i - w_i rho_ref towards the Eq. 4 equilibrium at u + F/(omega rho),
+// written as deviations again:
+//   g*_i = (1 - omega) g_i + omega w_i d + omega w_i rho (3 c.u + 9/2 (c.u)^2 - 3/2 u^2)
+// with d = rho - rho_ref. OM1 drops the (1 - omega) g_i terms (omega = 1,
+// the paper's tau = 1). Returns d.
+template <bool OM1, typename T>
+__device__ __forceinline__ float collide(const float f[9], float Fx, float Fy,
+                                         const StepArgs<T>& a, float gs[9])
+{
+    const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const float rho = a.rho_ref + d;
+    const float inv = __frcp_rn(rho);
+    const float ux = fmaf(Fx, a.inv_omega, jx) * inv;
+    const float uy = fmaf(Fy, a.inv_omega, jy) * inv;
+    const float usq15 = 1.5f * fmaf(ux, ux, uy * uy);
+    const float orho = OM1 ? rho : a.omega * rho;
+    const float od = OM1 ? d : a.omega * d;
+    const float A0 = orho * a.w0, A1 = orho * a.w1, A2 = orho * a.w2;
+    const float D0 = od * a.w0, D1 = od * a.w1, D2 = od * a.w2;
+    float e[9];
+    e[0] = fmaf(A0, -usq15, D0);
+    {
+        const float s = fmaf(4.5f * ux, ux, -usq15), t3 = 3.f * ux;
+        e[1] = fmaf(A1, s + t3, D1);
+        e[3] = fmaf(A1, s - t3, D1);
+    }
+    {
+        const float s = fmaf(4.5f * uy, uy, -usq15), t3 = 3.f * uy;
+        e[2] = fmaf(A1, s + t3, D1);
+        e[4] = fmaf(A1, s - t3, D1);
+    }
+    {
+        const float c = ux + uy;
+        const float s = fmaf(4.5f * c, c, -usq15), t3 = 3.f * c;
+        e[5] = fmaf(A2, s + t3, D2);
+        e[7] = fmaf(A2, s - t3, D2);
+    }
+    {
+        const float c = uy - ux;
+        const float s = fmaf(4.5f * c, c, -usq15), t3 = 3.f * c;
+        e[6] = fmaf(A2, s + t3, D2);
+        e[8] = fmaf(A2, s - t3, D2);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) gs[i] = OM1 ? e[i] : fmaf(a.omc, f[i], e[i]);
+    return d;
+}
+
+// psi(rho) - psi_ref = -sqrt(rho0) e^{-rho_ref/rho0} expm1(-(rho - rho_ref)/rho0)
+template <typename T>
+__device__ __forceinline__ float dpsi_of(float d, const StepArgs<T>& a)
+{
+    return a.cpsi * expm1f(-d * a.inv_rho0);
+}
+
+// Deterministic sum of 4 doubles over a CTA of NT threads (NT a multiple of
+// 32, at most 1024); the result is valid in thread 0.
+template <int NT>
+__device__ void block_sum4(double v[4])
+{
+    __shared__ double red[NT / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) red[warp][k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < NT / 32; ++w) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] += red[w][k];
+        }
+    }
+    __syncthreads();
+}
+
+// Store this CTA's partial, and if it is the last CTA to arrive, sum all
+// partials (each thread a fixed strided subset, then a fixed tree) and return
+// true in thread 0 with the total in v. Resets the counter for the next use.
+template <int NT>
+__device__ bool last_block_total(double v[4], double* partials, unsigned int* counter,
+                                 unsigned int nblocks)
+{
+    __shared__ bool s_last;
+    const unsigned int b = blockIdx.y * gridDim.x + blockIdx.x;
+    block_sum4<NT>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) partials[4 * (size_t)b + k] = v[k];
+        __threadfence();
+        const unsigned int prev = atomicAdd(counter, 1u);
+        s_last = (prev == nblocks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    for (unsigned int j = threadIdx.x; j < nblocks; j += NT) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] += __ldcg(partials + 4 * (size_t)j + k);
+    }
+    block_sum4<NT>(w);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = w[k];
+        *counter = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
+__device__ __forceinline__ void write_trace_row(double* trace, int* trace_count, long long t,
+                                                double mass, double es, double em, double eb)
+{
+    const int c = *trace_count;
+    double* row = trace + (size_t)(c % kTraceCap) * kTraceCols;
+    row[0] = (double)t;
+    row[1] = mass;
+    row[2] = es;
+    row[3] = em;
+    row[4] = eb;
+    *trace_count = c + 1;
+}
+
+}  // namespace dev
+}  // namespace lbsc

@@ -30,96 +30,14 @@
 // state t (FP32 per thread for 16 rows, then FP64), reduce them per CTA in
 // FP64 and let the last CTA to finish sum all CTA partials in a fixed order
 // into one trace row — deterministic for a given launch shape.
-#include "lb_internal.h"
+#include "lb_device.cuh"
 
 #include <cmath>
 
 namespace lbsc {
 namespace {
 
-__device__ __forceinline__ float ldg_(const float* p) { return __ldg(p); }
-__device__ __forceinline__ float ldg_(const __half* p) { return __half2float(__ldg(p)); }
-__device__ __forceinline__ void st_(float* p, float v) { *p = v; }
-__device__ __forceinline__ void st_(__half* p, float v) { *p = __float2half_rn(v); }
-
-__device__ __forceinline__ int wrapi(int a, int n)
-{
-    a %= n;
-    return a < 0 ? a + n : a;
-}
-
-// Deterministic sum of 4 doubles over a CTA of NT threads (NT a multiple of
-// 32, at most 1024); the result is valid in thread 0.
-template <int NT>
-__device__ void block_sum4(double v[4])
-{
-    __shared__ double red[NT / 32][4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) red[warp][k] = v[k];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < NT / 32; ++w) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] += red[w][k];
-        }
-    }
-    __syncthreads();
-}
-
-// Store this CTA's partial, and if it is the last CTA to arrive, sum all
-// partials (each thread a fixed strided subset, then a fixed tree) and return
-// true in thread 0 with the total in v. Resets the counter for the next use.
-template <int NT>
-__device__ bool last_block_total(double v[4], double* partials, unsigned int* counter,
-                                 unsigned int nblocks)
-{
-    __shared__ bool s_last;
-    const unsigned int b = blockIdx.y * gridDim.x + blockIdx.x;
-    block_sum4<NT>(v);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) partials[4 * (size_t)b + k] = v[k];
-        __threadfence();
-        const unsigned int prev = atomicAdd(counter, 1u);
-        s_last = (prev == nblocks - 1);
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    double w[4] = {0.0, 0.0, 0.0, 0.0};
-    for (unsigned int j = threadIdx.x; j < nblocks; j += NT) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) w[k] += __ldcg(partials + 4 * (size_t)j + k);
-    }
-    block_sum4<NT>(w);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = w[k];
-        *counter = 0u;
-    }
-    return threadIdx.x == 0;
-}
-
-__device__ __forceinline__ void write_trace_row(double* trace, int* trace_count, long long t,
-                                                double mass, double es, double em, double eb)
-{
-    const int c = *trace_count;
-    double* row = trace + (size_t)(c % kTraceCap) * kTraceCols;
-    row[0] = (double)t;
-    row[1] = mass;
-    row[2] = es;
-    row[3] = em;
-    row[4] = eb;
-    *trace_count = c + 1;
-}
+using namespace dev;
 
 // Pull f_i(x, r) = f*_i(x - c_i, r - c_iy) for the 9 D2Q9 speeds in the order
 // (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
@@ -139,7 +57,30 @@ __device__ __forceinline__ void pull(float f[9], const T* __restrict__ g, long l
     f[8] = ldg_(g + 8 * N + op + xm);
 }
 
-template <typename T, int BX, bool REDUCE>
+// The same pull with 32-bit element offsets (9 N < 2^31 is enforced at init).
+template <typename T>
+__device__ __forceinline__ void pull32(float f[9], const T* __restrict__ g, int N, int om, int oc,
+                                       int op, int xm, int xc, int xp)
+{
+    f[0] = ldg_(g + (oc + xc));
+    f[1] = ldg_(g + (N + oc + xm));
+    f[2] = ldg_(g + (2 * N + om + xc));
+    f[3] = ldg_(g + (3 * N + oc + xp));
+    f[4] = ldg_(g + (4 * N + op + xc));
+    f[5] = ldg_(g + (5 * N + om + xm));
+    f[6] = ldg_(g + (6 * N + om + xp));
+    f[7] = ldg_(g + (7 * N + op + xp));
+    f[8] = ldg_(g + (8 * N + op + xm));
+}
+
+// Advance a row offset (row * nx) by one row with periodic wrap.
+__device__ __forceinline__ int next_row(int off, int nx, int N)
+{
+    off += nx;
+    return off == N ? 0 : off;
+}
+
+template <typename T, int BX, bool REDUCE, bool OM1>
 __global__ void __launch_bounds__(BX) k_step(const StepArgs<T> a)
 {
     constexpr int W = BX + 4;
@@ -149,7 +90,7 @@ __global__ void __launch_bounds__(BX) k_step(const StepArgs<T> a)
 
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
-    const long long N = a.N;
+    const int N = (int)a.N;
     const int x0 = blockIdx.x * (BX - 2);
     const int y0 = blockIdx.y * a.rows;
     const int y1 = min(y0 + a.rows, ny);
@@ -163,17 +104,20 @@ __global__ void __launch_bounds__(BX) k_step(const StepArgs<T> a)
 
     // dpsi rows y0-3 .. y0+1 into the ring
     for (int rr = y0 - 3; rr <= y0 + 1; ++rr) {
-        const float* src = a.dpsi_in + (long long)wrapi(rr, ny) * nx;
+        const float* src = a.dpsi_in + wrapi(rr, ny) * nx;
         win[rr & 7][tid] = __ldg(src + pc0);
         if (tid < 4) win[rr & 7][BX + tid] = __ldg(src + pc1);
     }
+    // Row offsets (row * nx, periodic) kept incrementally, no division in the
+    // loop: at the top of iteration r, o0, o1, o2 hold rows r-1, r, r+1 and oq
+    // holds row r+3 (the dpsi row prefetched into the ring).
+    int o0 = wrapi(y0 - 2, ny) * nx;
+    int o1 = wrapi(y0 - 1, ny) * nx;
+    int o2 = wrapi(y0, ny) * nx;
+    int oq = wrapi(y0 + 2, ny) * nx;
 
     float f[9];
-    {
-        const int r = y0 - 1;
-        pull(f, a.g_in, N, (long long)wrapi(r - 1, ny) * nx, (long long)wrapi(r, ny) * nx,
-             (long long)wrapi(r + 1, ny) * nx, xm, xc, xp);
-    }
+    pull32(f, a.g_in, N, o0, o1, o2, xm, xc, xp);   // collision row y0 - 1
     __syncthreads();
 
     float acc_m = 0.f, acc_0 = 0.f;
@@ -185,104 +129,34 @@ __global__ void __launch_bounds__(BX) k_step(const StepArgs<T> a)
         const bool need_psi = r <= y1 - 1;
         float pn0 = 0.f, pn1 = 0.f;
         if (need_psi) {
-            const float* src = a.dpsi_in + (long long)wrapi(r + 3, ny) * nx;
+            const float* src = a.dpsi_in + oq;
             pn0 = __ldg(src + pc0);
             if (tid < 4) pn1 = __ldg(src + pc1);
         }
+        oq = next_row(oq, nx, N);
+        // rows r, r+1, r+2: the pull of collision row r+1
+        o0 = o1;
+        o1 = o2;
+        o2 = next_row(o2, nx, N);
         float fn[9];
-        if (r < y1) {
-            pull(fn, a.g_in, N, (long long)wrapi(r, ny) * nx, (long long)wrapi(r + 1, ny) * nx,
-                 (long long)wrapi(r + 2, ny) * nx, xm, xc, xp);
-        }
+        if (r < y1) pull32(fn, a.g_in, N, o0, o1, o2, xm, xc, xp);
 
-        // ---- force from the dpsi(t) ring (Eq. FORCE, pair form)
-        const float* rM2 = &win[(r - 2) & 7][tid + 2];
-        const float* rM1 = &win[(r - 1) & 7][tid + 2];
-        const float* rC = &win[r & 7][tid + 2];
-        const float* rP1 = &win[(r + 1) & 7][tid + 2];
-        const float* rP2 = &win[(r + 2) & 7][tid + 2];
-        const float pc = a.psi_ref + rC[0];
+        // ---- force from the dpsi(t) ring, then moments and collision
+        const float* rows[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) rows[k] = &win[(r - 2 + k) & 7][tid + 2];
+        const float pc = a.psi_ref + rows[2][0];
         float Sx, Sy;
-        {
-            const float d10 = rC[1] - rC[-1];
-            const float d01 = rP1[0] - rM1[0];
-            const float d11 = rP1[1] - rM1[-1];   // (1,1) - (-1,-1)
-            const float d1m = rM1[1] - rP1[-1];   // (1,-1) - (-1,1)
-            const float d20 = rC[2] - rC[-2];
-            const float d02 = rP2[0] - rM2[0];
-            const float da = rP1[2] - rM1[-2];    // (2,1) - (-2,-1)
-            const float db = rP2[1] - rM2[-1];    // (1,2) - (-1,-2)
-            const float dc = rP2[-1] - rM2[1];    // (-1,2) - (1,-2)
-            const float dd = rP1[-2] - rM1[2];    // (-2,1) - (2,-1)
-            const float e1 = rP2[2] - rM2[-2];    // (2,2) - (-2,-2)
-            const float e2 = rM2[2] - rP2[-2];    // (2,-2) - (-2,2)
-            Sx = a.K1 * d10 + a.K2 * (d11 + d1m) + 2.f * a.K4 * d20 +
-                 a.K5 * (2.f * (da - dd) + (db - dc)) + 2.f * a.K8 * (e1 + e2);
-            Sy = a.K1 * d01 + a.K2 * (d11 - d1m) + 2.f * a.K4 * d02 +
-                 a.K5 * ((da + dd) + 2.f * (db + dc)) + 2.f * a.K8 * (e1 - e2);
-        }
-        const float Fx = -pc * Sx;
-        const float Fy = -pc * Sy;
-
-        // ---- moments and BGK collision at the shifted velocity (Eqs. 2-4)
-        const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-        const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        const float rho = a.rho_ref + d;
-        const float inv = __frcp_rn(rho);
-        const float ux = fmaf(Fx, a.inv_omega, jx) * inv;
-        const float uy = fmaf(Fy, a.inv_omega, jy) * inv;
-        const float usq15 = 1.5f * fmaf(ux, ux, uy * uy);
-        const float orho = a.omega * rho;
-        const float A0 = orho * a.w0, A1 = orho * a.w1, A2 = orho * a.w2;
-        const float od = a.omega * d;
-        const float D0 = od * a.w0, D1 = od * a.w1, D2 = od * a.w2;
-        const float omc = a.omc;
+        force_sums(rows, a, Sx, Sy);
         float gs[9];
-        gs[0] = fmaf(omc, f[0], fmaf(A0, -usq15, D0));
-        {
-            const float s = fmaf(4.5f * ux, ux, -usq15), t3 = 3.f * ux;
-            gs[1] = fmaf(omc, f[1], fmaf(A1, s + t3, D1));
-            gs[3] = fmaf(omc, f[3], fmaf(A1, s - t3, D1));
-        }
-        {
-            const float s = fmaf(4.5f * uy, uy, -usq15), t3 = 3.f * uy;
-            gs[2] = fmaf(omc, f[2], fmaf(A1, s + t3, D1));
-            gs[4] = fmaf(omc, f[4], fmaf(A1, s - t3, D1));
-        }
-        {
-            const float c = ux + uy;
-            const float s = fmaf(4.5f * c, c, -usq15), t3 = 3.f * c;
-            gs[5] = fmaf(omc, f[5], fmaf(A2, s + t3, D2));
-            gs[7] = fmaf(omc, f[7], fmaf(A2, s - t3, D2));
-        }
-        {
-            const float c = uy - ux;
-            const float s = fmaf(4.5f * c, c, -usq15), t3 = 3.f * c;
-            gs[6] = fmaf(omc, f[6], fmaf(A2, s + t3, D2));
-            gs[8] = fmaf(omc, f[8], fmaf(A2, s - t3, D2));
-        }
+        const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
 
-        const bool out_row = r >= y0 && r < y1;
-        if (out_col && out_row) {
-            T* o = a.g_out + (long long)r * nx + xc;
+        if (out_col && r >= y0 && r < y1) {
+            T* o = a.g_out + (r * nx + xc);
 #pragma unroll
             for (int i = 0; i < 9; ++i) st_(o + i * N, gs[i]);
             if (REDUCE) {
-                // Sec. 5 pseudo-energies of state t at (x, r), psi = psi_ref + dpsi
-                const float pr = a.psi_ref;
-                const float S1 = (rC[1] + rC[-1]) + (rP1[0] + rM1[0]);
-                const float S2 = (rP1[1] + rP1[-1]) + (rM1[1] + rM1[-1]);
-                const float S4 = (rC[2] + rC[-2]) + (rP2[0] + rM2[0]);
-                const float S5 = ((rP1[2] + rP1[-2]) + (rM1[2] + rM1[-2])) +
-                                 ((rP2[1] + rP2[-1]) + (rM2[1] + rM2[-1]));
-                const float S8 = (rP2[2] + rP2[-2]) + (rM2[2] + rM2[-2]);
-                const float b1 = a.K0 * pc + a.K1 * fmaf(4.f, pr, S1) + a.K2 * fmaf(4.f, pr, S2);
-                const float b2 = a.K4 * fmaf(4.f, pr, S4) + a.K5 * fmaf(8.f, pr, S5) +
-                                 a.K8 * fmaf(4.f, pr, S8);
-                es = fmaf(0.5f * pc, b1, es);
-                em = fmaf(0.5f * pc, b2, em);
-                eb = fmaf(a.half_A1 * pc, pc, eb);
+                energy_site(rows, pc, a, es, em, eb);
                 ms += d;
                 if (((r - y0) & 15) == 15) {
                     d_es += es; d_em += em; d_eb += eb; d_ms += ms;
@@ -304,10 +178,7 @@ __global__ void __launch_bounds__(BX) k_step(const StepArgs<T> a)
         acc_m += gs[4] + (R.x + L.x);
         acc_0 += gs[0] + (R.y + L.y);
         const float acc_p = gs[2] + (R.z + L.z);
-        if (out_col && r - 1 >= y0) {
-            // psi(t+1) - psi_ref = -sqrt(rho0) e^{-rho_ref/rho0} expm1(-(rho - rho_ref)/rho0)
-            a.dpsi_out[(long long)(r - 1) * nx + xc] = a.cpsi * expm1f(-acc_m * a.inv_rho0);
-        }
+        if (out_col && r - 1 >= y0) a.dpsi_out[(r - 1) * nx + xc] = dpsi_of(acc_m, a);
         acc_m = acc_0;
         acc_0 = acc_p;
 #pragma unroll
@@ -441,10 +312,14 @@ template <typename T, int BX>
 cudaError_t launch_step_bx(const StepArgs<T>& a, Fp32Launch L, bool reduce, cudaStream_t s)
 {
     dim3 grid((a.nx + BX - 3) / (BX - 2), (a.ny + L.rows - 1) / L.rows);
-    if (reduce)
-        k_step<T, BX, true><<<grid, BX, 0, s>>>(a);
-    else
-        k_step<T, BX, false><<<grid, BX, 0, s>>>(a);
+    const bool om1 = a.omega == 1.0f;
+    if (reduce) {
+        if (om1) k_step<T, BX, true, true><<<grid, BX, 0, s>>>(a);
+        else k_step<T, BX, true, false><<<grid, BX, 0, s>>>(a);
+    } else {
+        if (om1) k_step<T, BX, false, true><<<grid, BX, 0, s>>>(a);
+        else k_step<T, BX, false, false><<<grid, BX, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -44,16 +44,26 @@ struct StepArgs {
     double* trace;                   // [kTraceCap][5] ring
     int* trace_count;                // rows ever written
     long long t;                     // time level of the reduced state
+    // bounded waits of the bulk-copy kernel
+    int* err;                        // set to nonzero when a wait runs out
+    long long wait_cycles;           // clock limit of one wait
+    unsigned int extra_tx;           // test hook: bytes a unit's barrier expects beyond its copies
 };
 
 // Launchers (lb_fp32.cu). All return the launch's cudaError_t.
 struct Fp32Launch {
-    int block_x;   // threads per CTA = columns per CTA including the 2 halo columns
+    int block_x;   // threads per CTA
     int rows;      // output rows per CTA
+    int pipeline;  // 0: register-prefetch pull (any shape), 1: bulk-copy rings (aligned shapes)
 };
 int fp32_grid_blocks(int nx, int ny, Fp32Launch L);
 cudaError_t fp32_step(const StepArgs<float>& a, Fp32Launch L, bool reduce, cudaStream_t s);
 cudaError_t fp16_step(const StepArgs<__half>& a, Fp32Launch L, bool reduce, cudaStream_t s);
+// bulk-copy pipelined step (lb_bulk.cu)
+bool bulk_supported(int nx, int ny, int elem_bytes, int block_x);
+int bulk_grid_blocks(int nx, int ny, int elem_bytes, Fp32Launch L);
+cudaError_t fp32_step_bulk(const StepArgs<float>& a, Fp32Launch L, bool reduce, cudaStream_t s);
+cudaError_t fp16_step_bulk(const StepArgs<__half>& a, Fp32Launch L, bool reduce, cudaStream_t s);
 template <typename T>
 cudaError_t delta_init(T* g, float* dpsi, const double* rho_init, int nx, int ny,
                        double rho_ref, double rho0, cudaStream_t s);

@@ -51,7 +51,7 @@ def test_params_struct_layout_matches_header(lib):
 
 
 def test_status_strings(lib):
-    for st in (0, -1, -2, -3, -4, -5):
+    for st in (0, -1, -2, -3, -4, -5, -6):
         assert capi.lb_status_str(st)
     assert capi.lb_status_str(17) == "unknown status"
 

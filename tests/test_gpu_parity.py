@@ -20,6 +20,19 @@ def _norm_err(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
+def _trace_err(tr, ref):
+    """Largest relative deviation of energy/mass columns; a column that is exactly
+    zero in the reference (E_m when G2 = 0) must be zero here too."""
+    worst = 0.0
+    for c in range(1, 5):
+        r = ref[:, c]
+        if np.all(r == 0):
+            worst = max(worst, float(np.max(np.abs(tr[:, c]))))
+        else:
+            worst = max(worst, float(np.max(np.abs(tr[:, c] - r) / np.abs(r))))
+    return worst
+
+
 def _run_gpu(rho0, steps, prec="fp32", launch=None, **kw):
     with Lattice(rho0, prec=prec, **kw) as lat:
         if launch:
@@ -43,7 +56,7 @@ def test_fp64_1000_steps_128(G2):
     assert _norm_err(ux, ref[1]) <= 1e-12 and _norm_err(uy, ref[2]) <= 1e-12
     assert tr.shape == ref[3].shape == (100, 5)
     assert np.array_equal(tr[:, 0], ref[3][:, 0])
-    assert np.max(np.abs(tr[:, 1:] - ref[3][:, 1:]) / np.abs(ref[3][:, 1:])) <= 1e-12
+    assert _trace_err(tr, ref[3]) <= 1e-12
     # phase separation happened: this is not a near-uniform comparison
     assert rho.max() > 1.5 and rho.min() < 0.3
 
@@ -60,39 +73,47 @@ def test_fp64_is_bit_exact_over_short_runs():
 
 # ----------------------------------------------------------------- FP32 parity
 FP32_CASES = [
-    # (nx, ny, G2, omega, noise mode, seed)
-    (128, 128, 0.0, 1.0, "abs", 1),
-    (128, 128, 0.5, 1.0, "abs", 1),
-    (300, 200, 0.6, 1.0, "rel", 2),     # 3 ragged strips, ragged last row chunk
-    (131, 67, 0.9, 1.0, "rel", 3),
-    (256, 256, 0.3, 1.3, "rel", 4),     # omega != 1 exercises (1 - omega) f
-    (5, 5, 0.5, 1.0, "abs", 5),         # smallest lattice the stencil allows
-    (6, 7, 0.0, 0.9, "abs", 6),
-    (1024, 40, 0.6, 1.0, "rel", 8),     # many strips, one short chunk
+    # (nx, ny, G2, omega, noise mode, seed, steps)
+    (128, 128, 0.0, 1.0, "abs", 1, 100),
+    (128, 128, 0.5, 1.0, "abs", 1, 100),
+    (300, 200, 0.6, 1.0, "rel", 2, 100),     # 3 ragged strips, ragged last row chunk
+    (131, 67, 0.9, 1.0, "rel", 3, 100),
+    (256, 256, 0.3, 1.3, "rel", 4, 100),     # omega != 1 exercises (1 - omega) f
+    (1024, 40, 0.6, 1.0, "rel", 8, 100),     # many strips, one short chunk
+    # Lattices too small for any unstable mode: the noise decays and u -> 0
+    # (1e-17 after 100 steps), so max|u| cannot normalise the error there; they
+    # are compared while the flow is still O(1e-4).
+    (5, 5, 0.5, 1.0, "abs", 5, 10),          # smallest lattice the stencil allows
+    (6, 7, 0.0, 0.9, "abs", 6, 10),
+    (5, 9, 0.6, 1.0, "abs", 7, 10),
 ]
 
 
-@pytest.mark.parametrize("nx,ny,G2,omega,mode,seed", FP32_CASES)
-def test_fp32_100_steps(nx, ny, G2, omega, mode, seed):
+@pytest.mark.parametrize("nx,ny,G2,omega,mode,seed,steps", FP32_CASES)
+def test_fp32_parity(nx, ny, G2, omega, mode, seed, steps):
     rho0 = inputs.noisy_density(nx, ny, seed=seed, mean=0.7, amp=0.01, mode=mode)
-    ref = oracle.run(rho0, 100, omega=omega, G1=-5.0, G2=G2, trace_every=10)
-    rho, ux, uy, tr, en = _run_gpu(rho0, 100, omega=omega, G1=-5.0, G2=G2, trace_every=10)
+    ref = oracle.run(rho0, steps, omega=omega, G1=-5.0, G2=G2, trace_every=10)
+    rho, ux, uy, tr, en = _run_gpu(rho0, steps, omega=omega, G1=-5.0, G2=G2, trace_every=10)
     assert _norm_err(rho, ref[0]) <= 1e-5
     assert _norm_err(ux, ref[1]) <= 1e-5 and _norm_err(uy, ref[2]) <= 1e-5
     assert np.array_equal(tr[:, 0], ref[3][:, 0])
     assert np.max(np.abs(tr[:, 1] - ref[3][:, 1]) / ref[3][:, 1]) <= 1e-6          # mass
-    assert np.max(np.abs(tr[:, 2:] - ref[3][:, 2:]) / np.abs(ref[3][:, 2:])) <= 1e-4
+    assert _trace_err(tr, ref[3]) <= 1e-4
 
 
-@pytest.mark.parametrize("launch", [(64, 16), (96, 17), (128, 16), (192, 40), (256, 33)])
-def test_fp32_launch_shapes_agree(launch):
-    """Every CTA shape gives the same trajectory (tile edges, halo columns, ragged tails)."""
-    rho0 = inputs.noisy_density(301, 170, seed=9, mean=0.7, amp=0.01, mode="rel")
+@pytest.mark.parametrize("nx,launch", [(301, (64, 16, 0)), (301, (96, 17, 0)), (301, (128, 16, 0)),
+                                       (301, (192, 40, 0)), (301, (256, 33, 0)),
+                                       (300, (64, 16, 1)), (300, (128, 23, 1)),
+                                       (300, (256, 40, 1)), (512, (128, 64, 1))])
+def test_fp32_launch_shapes_agree(nx, launch):
+    """Every CTA shape and both pipelines give the trajectory of the oracle (tile edges,
+    halo columns, ragged strips and row chunks, periodic wrap of the copy windows)."""
+    rho0 = inputs.noisy_density(nx, 170, seed=9, mean=0.7, amp=0.01, mode="rel")
     ref = oracle.run(rho0, 60, G1=-5.0, G2=0.6, trace_every=10)
     rho, ux, uy, tr, _ = _run_gpu(rho0, 60, launch=launch, G1=-5.0, G2=0.6, trace_every=10)
     assert _norm_err(rho, ref[0]) <= 1e-5
     assert _norm_err(ux, ref[1]) <= 1e-5 and _norm_err(uy, ref[2]) <= 1e-5
-    assert np.max(np.abs(tr[:, 2:] - ref[3][:, 2:]) / np.abs(ref[3][:, 2:])) <= 1e-4
+    assert _trace_err(tr, ref[3]) <= 1e-4
 
 
 def test_fp32_energy_entry_matches_oracle_energy():
@@ -193,9 +214,13 @@ def test_step_arguments_and_time():
         lat.step(7)
         assert lat.t == 7
         with pytest.raises(LBError):
-            lat.set_launch(100, 16)
+            lat.set_launch(100, 16, 0)
         with pytest.raises(LBError):
-            lat.set_launch(128, 8)
+            lat.set_launch(128, 8, 0)
+        with pytest.raises(LBError):
+            lat.set_launch(128, 16, 1)      # nx = 16 is too narrow for the copy windows
+        with pytest.raises(LBError):
+            lat.set_launch(128, 16, 2)
 
 
 def test_device_pointers_and_partial_fields():
@@ -210,6 +235,36 @@ def test_device_pointers_and_partial_fields():
         only_ux = np.empty((30, 40))
         lat.fields(ux=only_ux)
         assert np.array_equal(only_ux, h_ux)
+
+
+def test_default_pipeline_choice():
+    with Lattice(inputs.noisy_density(512, 64, seed=1)) as lat:
+        assert lat.launch[2] == 1                  # aligned and wide: bulk-copy rings
+    with Lattice(inputs.noisy_density(301, 64, seed=1)) as lat:
+        assert lat.launch[2] == 0                  # odd width: register prefetch
+    with Lattice(inputs.noisy_density(516, 64, seed=1), prec="fp16_delta") as lat:
+        assert lat.launch[2] == 0                  # fp16 rows need 8-element alignment
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A barrier that expects bytes no copy delivers makes every wait run out; the
+    kernel returns, the next synchronising call reports LB_ERR_TIMEOUT, and the
+    CUDA context keeps working for a fresh state."""
+    rho0 = inputs.noisy_density(256, 48, seed=2)
+    lat = Lattice(rho0, trace_every=0)
+    assert lat.launch[2] == 1
+    capi.lb_set_wait_limit(lat.handle, 2_000_000, 16)    # ~1 ms per wait
+    lat.step(1)
+    with pytest.raises(LBError) as ei:
+        lat.energy()
+    assert ei.value.status == capi.LB_ERR_TIMEOUT
+    with pytest.raises(LBError) as ei:
+        lat.step(1)
+    assert ei.value.status == capi.LB_ERR_STATE
+    lat.close()
+    ref = oracle.run(rho0, 20, G1=-5.0, G2=0.0)
+    rho, _, _, _, _ = _run_gpu(rho0, 20, G1=-5.0, G2=0.0, trace_every=0)
+    assert _norm_err(rho, ref[0]) <= 1e-5
 
 
 def test_trace_rows_and_ring():
