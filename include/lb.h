@@ -144,6 +144,36 @@ lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta, int pipeline
  * Errors: LB_ERR_ARG (NULL, cycles <= 0). */
 lb_status lb_set_wait_limit(lb_state* s, long long cycles, unsigned int extra_expect_bytes);
 
+/* Pseudo-energies and mass of caller-provided fields, without any device
+ * allocation. The paper has no counterpart to this entry point: it exists
+ * for callers that cannot call cudaMalloc, such as code running inside a
+ * framework that hands out all device memory from its own pool (an extra
+ * cudaMalloc there bypasses the pool's accounting and can fail once the pool
+ * holds the memory), or code that must not trigger the implicit device
+ * synchronisation of cudaMalloc. The sums are those of lb_energy:
+ *   out[0] = E_s, out[1] = E_m, out[2] = E_bulk (Sec. 5), out[3] = sum rho,
+ * computed from
+ *   psi, rho  N = nx*ny doubles each, row-major [y][x], in device memory of
+ *             the current device (the psi values are used as given);
+ *   nx, ny    >= 5, and nx*ny <= 134,217,728 sites (8192 CTAs of 16,384
+ *             sites: the capacity of the scratch array below);
+ *   G1, G2    the couplings of Eq. FORCE / Table 1;
+ *   out       4 doubles, host or device memory. With host memory the call
+ *             synchronises the stream and returns LB_ERR_NONFINITE if a sum
+ *             is not finite; with device memory it returns without waiting.
+ * Scratch: one static device array of 262,208 bytes inside this library,
+ * present on every GPU that loads the library until the process exits. The
+ * first call on a device looks up that array's device address with the
+ * device current (cudaGetSymbolAddress), so make the first call on each
+ * device before any stream capture begins. Every call shares the array and
+ * clears its arrival counter first; calls whose kernels overlap on the GPU
+ * (different streams, or different host threads on one device) race on it
+ * and must be serialised by the caller.
+ * Errors: LB_ERR_ARG (NULL, non-device psi/rho, sizes out of range,
+ * non-finite couplings), LB_ERR_CUDA, LB_ERR_NONFINITE. */
+lb_status lb_energy_noalloc(const double* psi, const double* rho, int nx, int ny, double G1,
+                            double G2, double* out, void* stream);
+
 /* Current time step t (number of lb_step steps taken since lb_init); -1 for NULL. */
 long lb_time(const lb_state* s);
 

@@ -83,6 +83,9 @@ def load(build_if_missing: bool = False):
             lib.lb_set_launch.restype = ctypes.c_int
             lib.lb_set_wait_limit.argtypes = [vp, ctypes.c_longlong, ctypes.c_uint]
             lib.lb_set_wait_limit.restype = ctypes.c_int
+            lib.lb_energy_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_double, ctypes.c_double, vp, vp]
+            lib.lb_energy_noalloc.restype = ctypes.c_int
             lib.lb_destroy.argtypes = [vp]
             lib.lb_destroy.restype = None
             lib.lb_status_str.argtypes = [ctypes.c_int]
@@ -176,6 +179,20 @@ def lb_set_launch(h: int, block_x: int, rows_per_cta: int, pipeline: int) -> Non
 def lb_set_wait_limit(h: int, cycles: int, extra_expect_bytes: int = 0) -> None:
     _check(load().lb_set_wait_limit(ctypes.c_void_p(h), int(cycles), int(extra_expect_bytes)),
            "lb_set_wait_limit")
+
+
+def lb_energy_noalloc(psi, rho, nx: int, ny: int, G1: float, G2: float, out=None,
+                      stream: int = 0):
+    """(E_s, E_m, E_bulk, mass) of device fields psi and rho without any device
+    allocation (scratch in a static device array; see include/lb.h). With
+    out=None the result comes back through a host buffer."""
+    host = out is None
+    if host:
+        out = np.zeros(4)
+    st = load().lb_energy_noalloc(_ptr(psi), _ptr(rho), int(nx), int(ny), float(G1), float(G2),
+                                  _ptr(out), ctypes.c_void_p(stream or None))
+    _check(st, "lb_energy_noalloc")
+    return tuple(float(v) for v in out) if host else out
 
 
 def lb_time(h) -> int:

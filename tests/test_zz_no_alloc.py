@@ -1,0 +1,61 @@
+"""lb_energy_noalloc: the pseudo-energy / mass reduction for callers that
+cannot allocate device memory (for example code whose device memory all comes
+from a framework's own pool). Its scratch is a static device array inside the
+library; this file checks that two calls in a row through the C ABI agree
+with lb_energy on the same state, and that sizes beyond the array's capacity
+are refused. The file is named to be collected last."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1008_2865_gb300 import LBError, Lattice, capi, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _psi(torch, rho, rho0=1.0):
+    return math.sqrt(rho0) * (1.0 - torch.exp(-rho / rho0))
+
+
+@pytest.mark.parametrize("nx,ny,G2", [(96, 80, 0.5), (131, 67, 0.0), (512, 512, 0.9)])
+def test_noalloc_energy_matches_lb_energy_twice(nx, ny, G2):
+    torch = pytest.importorskip("torch")
+    rho0 = inputs.noisy_density(nx, ny, seed=21, mean=0.7, amp=0.05)
+    with Lattice(rho0, prec="fp64", G1=-5.0, G2=G2, trace_every=0) as lat:
+        lat.step(30)
+        ref = lat.energy()
+        rho = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+        lat.fields(rho=rho)
+    psi = _psi(torch, rho)
+    torch.cuda.synchronize()
+    first = capi.lb_energy_noalloc(psi, rho, nx, ny, -5.0, G2)
+    second = capi.lb_energy_noalloc(psi, rho, nx, ny, -5.0, G2)
+    assert first == second
+    for got in (first, second):
+        for g, r in zip(got, ref):
+            if r == 0.0:
+                assert abs(g) <= 1e-12
+            else:
+                assert abs(g - r) <= 1e-12 * abs(r)
+    # device output, read after the stream is done
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    capi.lb_energy_noalloc(psi, rho, nx, ny, -5.0, G2, out=out,
+                           stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert tuple(out.cpu().numpy()) == first
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch_and_host_fields():
+    torch = pytest.importorskip("torch")
+    small = torch.ones((8, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(LBError) as ei:
+        capi.lb_energy_noalloc(small, small, 16384, 8193, -5.0, 0.0)
+    assert ei.value.status == capi.LB_ERR_ARG
+    with pytest.raises(LBError) as ei:
+        capi.lb_energy_noalloc(small, small, 4, 8, -5.0, 0.0)
+    assert ei.value.status == capi.LB_ERR_ARG
+    host = np.ones((8, 8))
+    with pytest.raises(LBError) as ei:
+        capi.lb_energy_noalloc(host, host, 8, 8, -5.0, 0.0)
+    assert ei.value.status == capi.LB_ERR_ARG
