@@ -58,15 +58,25 @@ def _peaks():
         return 6800.0, "fallback (6.8 TB/s, earlier GB300 copy measurement)"
 
 
-def _traffic_record(kernel_file, nx, ny):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+def _sources_sha256():
+    """Hashes of the sources the fused step kernels are built from."""
+    out = {}
+    for name in ("lb_fp32.cu", "lb_bulk.cu", "lb_device.cuh", "lb_internal.h"):
+        path = os.path.join(ROOT, "paper_1008_2865_gb300", "csrc", name)
+        with open(path, "rb") as fh:
+            out[name] = hashlib.sha256(fh.read()).hexdigest()
+    return out
+
+
+def _traffic_record(nx, ny, launch):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if the
+    kernel sources and launch shape are unchanged since it was taken (else None)."""
     rec_path = os.path.join(ROOT, "profiles", "step_fp32_traffic.json")
     try:
         with open(rec_path) as fh:
             rec = json.load(fh)
-        with open(kernel_file, "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
-        if rec.get("source_sha256") == sha and rec.get("nx") == nx and rec.get("ny") == ny:
+        if (rec.get("sources_sha256") == _sources_sha256() and rec.get("nx") == nx
+                and rec.get("ny") == ny and list(rec.get("launch", [])) == list(launch)):
             return float(rec["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -119,6 +129,62 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+BATCH_SIZES = (192, 384, 640)
+BATCH_PER_SIZE = 32
+
+
+def run_batched(steps, warmup, stream, dev):
+    """The 96-replica G2 sweep (32 each of 192^2, 384^2, 640^2; G2 ~ U[0, 1) seed 100;
+    seeds 1000..1095; G1 = -5, FP32): aggregate MLUPS of the batched launch (one launch
+    per step over all replicas, CUDA-graph replay) against running the same replicas
+    one after another, each a single-lattice state stepping on its own."""
+    import torch
+
+    from paper_1008_2865_gb300 import Batch, Lattice, inputs
+    sizes = [n for n in BATCH_SIZES for _ in range(BATCH_PER_SIZE)]
+    g2 = inputs.g2_sweep(len(sizes), seed=100)
+    rhos = [inputs.noisy_density(n, n, 1000 + i, mean=0.7, amp=0.01, mode="rel")
+            for i, n in enumerate(sizes)]
+    sites = sum(n * n for n in sizes)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    from paper_1008_2865_gb300 import tune
+    shape = tune.lookup_batch([r.shape for r in rhos]) or (128, 32)
+    with Batch(rhos, G1=G1, G2=list(g2), trace_every=TRACE_EVERY, device=dev,
+               stream=stream.cuda_stream) as b:
+        b.set_launch(shape[0], shape[1], 1)
+        b.step(max(warmup, 3) * TRACE_EVERY)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms_batch = e0.elapsed_time(e1)
+        launch = b.launch
+    lats = [Lattice(r, G1=G1, G2=float(g), trace_every=TRACE_EVERY, device=dev,
+                    stream=stream.cuda_stream) for r, g in zip(rhos, g2)]
+    for lat in lats:
+        lat.step(max(warmup, 3) * TRACE_EVERY)
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for lat in lats:
+        lat.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    for lat in lats:
+        lat.close()
+    return {"workload": "96 replicas: 32 each of 192^2, 384^2, 640^2 periodic lattices, "
+                        "G2 ~ U[0,1) (seed 100), seeds 1000..1095, G1=-5, FP32, trace every 10",
+            "sites": sites, "steps": steps,
+            "mlups": sites * steps / (ms_batch / 1e3) / 1e6,
+            "one_by_one_mlups": sites * steps / (ms_seq / 1e3) / 1e6,
+            "speedup_vs_one_by_one": ms_seq / ms_batch,
+            "launch": {"block_x": launch[0], "rows_per_cta": launch[1], "cuda_graph": bool(launch[2])},
+            "launches_per_step": "1 (+1 per-replica reduction every 10 steps)"}
 
 
 def cpu_baseline(seconds=12.0):
@@ -239,8 +305,7 @@ def run_ours(args):
     per_launch_s = ms / 1e3 / args.steps
     peak, peak_src = _peaks()
     achieved = (BYTES_PER_SITE if args.prec == "fp32" else 44) * N / per_launch_s / 1e9
-    traffic = _traffic_record(os.path.join(ROOT, "paper_1008_2865_gb300", "csrc", "lb_fp32.cu"),
-                              NX, NY)
+    traffic = _traffic_record(NX, NY, launch)
     bytes_per_site = BYTES_PER_SITE if args.prec == "fp32" else 44
 
     if args.skip_e2e:
@@ -268,9 +333,13 @@ def run_ours(args):
     lat2.close()
     e2e_value = N * args.steps * ws / dt_e2e / 1e6
 
+    batched = run_batched(args.steps, args.warmup, stream, dev) if not args.skip_batch else None
+
     out = None
     if rank == 0:
         cpu = cpu_baseline() if ws == 1 else None
+        if batched is not None:
+            batched["vs_plain_mlups"] = batched["mlups"] / value
         clocks = clk.summary()
         out = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
@@ -297,6 +366,7 @@ def run_ours(args):
                                 "read every 10 steps (D2H), lb_fields rho to pinned host (D2H)"},
             "gpu_launches": args.steps,
             "clocks": clocks,
+            "batched": batched,
         }
     if ws > 1:
         import torch.distributed as dist
@@ -319,6 +389,8 @@ def main():
     ap.add_argument("--launch", default=None, help="block_x,rows_per_cta,pipeline override")
     ap.add_argument("--skip-e2e", action="store_true",
                     help="time the device-resident steps only and print a short line")
+    ap.add_argument("--skip-batch", action="store_true",
+                    help="leave out the batched 96-replica sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

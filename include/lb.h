@@ -126,7 +126,8 @@ lb_status lb_trace(lb_state* s, double* buf, int cap, int* count);
  *   1  bulk-copy rings: the bulk-copy (TMA) engine stages whole rows in shared
  *      memory several rows ahead (block_x in {64, 128, 256}; needs nx a
  *      multiple of 16 bytes' worth of elements and nx >= block_x + 8).
- * lb_init picks pipeline 1 where the shape allows it. rows_per_cta is in
+ * lb_init starts with pipeline 0 (measured the faster of the two on GB300 for
+ * the 8192 x 8192 lattice). rows_per_cta is in
  * [16, 4096]. The shape changes how the work is split, not the trajectory;
  * only the FP32 rounding of the energy partial sums depends on it.
  * Errors: LB_ERR_ARG for NULL or unsupported values, LB_ERR_STATE for an FP64
@@ -143,6 +144,41 @@ lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta, int pipeline
  * its copies deliver, so the waits run out on purpose; use 0 otherwise.
  * Errors: LB_ERR_ARG (NULL, cycles <= 0). */
 lb_status lb_set_wait_limit(lb_state* s, long long cycles, unsigned int extra_expect_bytes);
+
+/* ---- Batches: many independent lattices advanced by one launch per step ----
+ * A batch holds `count` replicas (each with its own size, couplings, omega,
+ * rho_ref and initial density; all with the same prec — LB_FP32 or
+ * LB_FP16_DELTA —, trace_every and device), e.g. a G2 sweep with distinct
+ * seeds. lb_batch_step advances all of them: one persistent launch per step
+ * strides over a work list of every replica's tiles, and steps are replayed
+ * from a CUDA graph of one trace period when the batch time is aligned to it.
+ * A replica's fields, energies and trace are bit-identical to those of the
+ * same lattice run alone with the same launch shape (register-prefetch
+ * pipeline). The paper runs its A2 scan (Sec. 4) as separate simulations;
+ * batching is this library's way to run such sweeps on one GPU.
+ *   params    array of count parameter sets (validated as in lb_init)
+ *   rho_init  array of count pointers to N_r initial densities (host or device)
+ * Errors: LB_ERR_ARG (count < 1, mixed prec/trace_every/device, FP64, or any
+ * lb_init error), LB_ERR_OOM, LB_ERR_CUDA. */
+typedef struct lb_batch lb_batch;
+lb_status lb_batch_init(lb_batch** out, int count, const lb_params* params,
+                        const double* const* rho_init, void* stream);
+/* Advance every replica n >= 0 steps (asynchronous). */
+lb_status lb_batch_step(lb_batch* b, long n);
+/* lb_energy / lb_fields / lb_trace of replica `replica` (0 <= replica < count). */
+lb_status lb_batch_energy(lb_batch* b, int replica, double out[4]);
+lb_status lb_batch_fields(lb_batch* b, int replica, double* rho, double* ux, double* uy);
+lb_status lb_batch_trace(lb_batch* b, int replica, double* buf, int cap, int* count);
+/* Tile shape shared by all replicas (block_x in {64, 96, 128, 192, 256},
+ * rows_per_cta in [16, 4096]) and whether steps replay from a CUDA graph
+ * (use_graph 0 or 1). Defaults: 128, 32, 1. */
+lb_status lb_batch_get_launch(const lb_batch* b, int* block_x, int* rows_per_cta, int* use_graph);
+lb_status lb_batch_set_launch(lb_batch* b, int block_x, int rows_per_cta, int use_graph);
+/* Number of replicas (-1 for NULL) and steps taken (-1 for NULL). */
+int lb_batch_count(const lb_batch* b);
+long lb_batch_time(const lb_batch* b);
+/* Free the batch and its replicas; NULL is a no-op. */
+void lb_batch_destroy(lb_batch* b);
 
 /* Pseudo-energies and mass of caller-provided fields, without any device
  * allocation. The paper has no counterpart to this entry point: it exists

@@ -10,6 +10,9 @@ from __future__ import annotations
 import numpy as np
 
 from . import capi, inputs  # noqa: F401
+from .capi import (lb_batch_count, lb_batch_destroy, lb_batch_energy, lb_batch_fields,  # noqa: F401
+                   lb_batch_get_launch, lb_batch_init, lb_batch_set_launch, lb_batch_step,
+                   lb_batch_time, lb_batch_trace)
 from .capi import (LBError, lb_destroy, lb_energy, lb_fields, lb_get_launch,  # noqa: F401
                    lb_init, lb_set_launch, lb_set_wait_limit, lb_status_str, lb_step, lb_time,
                    lb_trace, make_params)
@@ -72,6 +75,74 @@ class Lattice:
     def close(self) -> None:
         if getattr(self, "handle", None):
             lb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many independent lattices advanced together (one launch per step for all).
+
+    >>> b = Batch([rho_a, rho_b], G2=[0.3, 0.6])      # per-replica values or scalars
+    >>> b.step(100); rho, ux, uy = b.fields(1)
+    """
+
+    def __init__(self, rho_list, omega=1.0, G1=-5.0, G2=0.0, rho0=1.0, prec="fp32",
+                 trace_every=10, rho_ref=0.0, device=0, stream=0):
+        n = len(rho_list)
+
+        def per(v):
+            return list(v) if isinstance(v, (list, tuple, np.ndarray)) else [v] * n
+
+        om, g1, g2, r0, rr = per(omega), per(G1), per(G2), per(rho0), per(rho_ref)
+        self.shapes = [tuple(r.shape) for r in rho_list]
+        params = [make_params(r.shape[1], r.shape[0], om[i], g1[i], g2[i], r0[i], prec,
+                              trace_every, rr[i], device) for i, r in enumerate(rho_list)]
+        self.handle = lb_batch_init(params, rho_list, stream)
+
+    def __len__(self):
+        return lb_batch_count(self.handle)
+
+    @property
+    def t(self) -> int:
+        return lb_batch_time(self.handle)
+
+    def step(self, n: int = 1) -> None:
+        lb_batch_step(self.handle, n)
+
+    def energy(self, i: int):
+        return lb_batch_energy(self.handle, i)
+
+    def fields(self, i: int, rho=None, ux=None, uy=None):
+        if rho is None and ux is None and uy is None:
+            ny, nx = self.shapes[i]
+            rho, ux, uy = np.empty((ny, nx)), np.empty((ny, nx)), np.empty((ny, nx))
+        lb_batch_fields(self.handle, i, rho, ux, uy)
+        return rho, ux, uy
+
+    def trace(self, i: int, cap: int = 65536):
+        return lb_batch_trace(self.handle, i, cap)
+
+    @property
+    def launch(self):
+        return lb_batch_get_launch(self.handle)
+
+    def set_launch(self, block_x: int, rows_per_cta: int, use_graph: int = 1) -> None:
+        lb_batch_set_launch(self.handle, block_x, rows_per_cta, use_graph)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lb_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -24,6 +24,7 @@ UNITS = {
     "lb_api.cu": [],
     "lb_fp32.cu": [],
     "lb_bulk.cu": [],
+    "lb_batch.cu": [],
     "lb_fp64.cu": ["--fmad=false"],
     "lb_noalloc.cu": [],
 }

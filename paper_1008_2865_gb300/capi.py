@@ -83,6 +83,28 @@ def load(build_if_missing: bool = False):
             lib.lb_set_launch.restype = ctypes.c_int
             lib.lb_set_wait_limit.argtypes = [vp, ctypes.c_longlong, ctypes.c_uint]
             lib.lb_set_wait_limit.restype = ctypes.c_int
+            lib.lb_batch_init.argtypes = [ctypes.POINTER(vp), ctypes.c_int,
+                                          ctypes.POINTER(lb_params), ctypes.POINTER(vp), vp]
+            lib.lb_batch_init.restype = ctypes.c_int
+            lib.lb_batch_step.argtypes = [vp, ctypes.c_long]
+            lib.lb_batch_step.restype = ctypes.c_int
+            lib.lb_batch_energy.argtypes = [vp, ctypes.c_int, dp]
+            lib.lb_batch_energy.restype = ctypes.c_int
+            lib.lb_batch_fields.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+            lib.lb_batch_fields.restype = ctypes.c_int
+            lib.lb_batch_trace.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int)]
+            lib.lb_batch_trace.restype = ctypes.c_int
+            lib.lb_batch_get_launch.argtypes = [vp, ip, ip, ip]
+            lib.lb_batch_get_launch.restype = ctypes.c_int
+            lib.lb_batch_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.lb_batch_set_launch.restype = ctypes.c_int
+            lib.lb_batch_count.argtypes = [vp]
+            lib.lb_batch_count.restype = ctypes.c_int
+            lib.lb_batch_time.argtypes = [vp]
+            lib.lb_batch_time.restype = ctypes.c_long
+            lib.lb_batch_destroy.argtypes = [vp]
+            lib.lb_batch_destroy.restype = None
             lib.lb_energy_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_double, ctypes.c_double, vp, vp]
             lib.lb_energy_noalloc.restype = ctypes.c_int
@@ -193,6 +215,69 @@ def lb_energy_noalloc(psi, rho, nx: int, ny: int, G1: float, G2: float, out=None
                                   _ptr(out), ctypes.c_void_p(stream or None))
     _check(st, "lb_energy_noalloc")
     return tuple(float(v) for v in out) if host else out
+
+
+def lb_batch_init(params_list, rho_list, stream: int = 0) -> int:
+    """Handle of a batch of len(params_list) replicas; rho_list[r] is [ny_r, nx_r] float64."""
+    n = len(params_list)
+    if n != len(rho_list):
+        raise ValueError("one initial density per parameter set")
+    P = (lb_params * n)(*params_list)
+    keep = [np.ascontiguousarray(r, dtype=np.float64) if isinstance(r, np.ndarray) else r
+            for r in rho_list]
+    ptrs = (ctypes.c_void_p * n)(*[_ptr(r) for r in keep])
+    h = ctypes.c_void_p()
+    _check(load().lb_batch_init(ctypes.byref(h), n, P, ptrs, ctypes.c_void_p(stream or None)),
+           "lb_batch_init")
+    return h.value
+
+
+def lb_batch_step(h: int, n: int) -> None:
+    _check(load().lb_batch_step(ctypes.c_void_p(h), int(n)), "lb_batch_step")
+
+
+def lb_batch_energy(h: int, replica: int):
+    out = (ctypes.c_double * 4)()
+    _check(load().lb_batch_energy(ctypes.c_void_p(h), int(replica), out), "lb_batch_energy")
+    return tuple(out)
+
+
+def lb_batch_fields(h: int, replica: int, rho=None, ux=None, uy=None) -> None:
+    _check(load().lb_batch_fields(ctypes.c_void_p(h), int(replica), _ptr(rho), _ptr(ux),
+                                  _ptr(uy)), "lb_batch_fields")
+
+
+def lb_batch_trace(h: int, replica: int, cap: int = 65536) -> np.ndarray:
+    buf = np.zeros((max(cap, 1), 5))
+    cnt = ctypes.c_int(0)
+    _check(load().lb_batch_trace(ctypes.c_void_p(h), int(replica),
+                                 buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(cap),
+                                 ctypes.byref(cnt)), "lb_batch_trace")
+    return buf[: cnt.value].copy()
+
+
+def lb_batch_get_launch(h: int):
+    bx, rows, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().lb_batch_get_launch(ctypes.c_void_p(h), ctypes.byref(bx), ctypes.byref(rows),
+                                      ctypes.byref(g)), "lb_batch_get_launch")
+    return bx.value, rows.value, g.value
+
+
+def lb_batch_set_launch(h: int, block_x: int, rows_per_cta: int, use_graph: int = 1) -> None:
+    _check(load().lb_batch_set_launch(ctypes.c_void_p(h), int(block_x), int(rows_per_cta),
+                                      int(use_graph)), "lb_batch_set_launch")
+
+
+def lb_batch_count(h) -> int:
+    return int(load().lb_batch_count(ctypes.c_void_p(h)))
+
+
+def lb_batch_time(h) -> int:
+    return int(load().lb_batch_time(ctypes.c_void_p(h)))
+
+
+def lb_batch_destroy(h) -> None:
+    load().lb_batch_destroy(ctypes.c_void_p(h))
 
 
 def lb_time(h) -> int:

@@ -30,35 +30,8 @@ Couplings couplings(double G1, double G2)
 
 }  // namespace lbsc
 
-struct lb_state {
-    lb_params p;
-    cudaStream_t stream = nullptr;
-    long long t = 0;
-    bool poisoned = false;
-    long long N = 0;
-    // FP32 / FP16 deviation storage
-    void* g[2] = {nullptr, nullptr};
-    float* dpsi[2] = {nullptr, nullptr};
-    int cur = 0;
-    double rho_ref = 0.0;
-    Fp32Launch launch{128, 64, 0};
-    int* err = nullptr;            // set by a kernel whose bounded wait ran out
-    long long wait_cycles = 2000000000LL;
-    unsigned int extra_tx = 0;
-    // FP64 parity storage
-    double* f64[2] = {nullptr, nullptr};
-    double* psi64 = nullptr;
-    double* rho64 = nullptr;
-    // reductions, trace, scratch
-    double* partials = nullptr;
-    size_t partials_cap = 0;       // number of 4-double partials
-    unsigned int* counter = nullptr;
-    double* trace = nullptr;
-    int* trace_count = nullptr;
-    double* res = nullptr;         // 4 doubles of results
-    int* flag = nullptr;
-    double* field_tmp = nullptr;   // N doubles, allocated on the first host-destined lb_fields
-};
+
+
 
 namespace {
 
@@ -89,19 +62,16 @@ lb_status validate(const lb_params* p)
     return LB_OK;
 }
 
-size_t elem_size(lb_precision p) { return p == LB_FP16_DELTA ? 2 : 4; }
-
-// Default launch shape: 128-thread strips, the bulk-copy pipeline where the
-// shape allows it, rows chosen for about four waves of the resident CTAs on a
-// 152-SM part (5 per SM with the rings, 8 without), at least 16 rows.
+// Default launch shape: 128-thread strips with the register-prefetch
+// pipeline (measured faster than the bulk-copy rings on GB300 for the 8192^2
+// lattice; the tuner may still pick the rings), rows chosen for about four
+// waves of 8 resident CTAs per SM on a 152-SM part, at least 16 rows.
 Fp32Launch default_launch(int nx, int ny, lb_precision prec)
 {
+    (void)prec;
     Fp32Launch L{128, 64, 0};
-    const int es = (int)elem_size(prec);
-    if (bulk_supported(nx, ny, es, 128)) L.pipeline = 1;
-    const int per = L.pipeline ? (es == 2 ? 120 : 124) : 126;
-    const long long strips = (nx + per - 1) / per;
-    const long long target = 152LL * (L.pipeline ? 5 : 8) * 4;
+    const long long strips = (nx + 125) / 126;
+    const long long target = 152LL * 8 * 4;
     long long rows = (strips * ny + target - 1) / target;
     if (rows < 16) rows = 16;
     if (rows > 512) rows = 512;
@@ -120,13 +90,23 @@ size_t step_blocks(const lb_state* s, Fp32Launch L)
 template <typename T>
 StepArgs<T> make_args(const lb_state* s)
 {
+    return lbsc::state_args<T>(s, s->cur);
+}
+
+}  // namespace
+
+namespace lbsc {
+
+template <typename T>
+StepArgs<T> state_args(const lb_state* s, int cur)
+{
     const lb_params& p = s->p;
     const Couplings K = couplings(p.G1, p.G2);
     StepArgs<T> a{};
-    a.g_in = static_cast<const T*>(s->g[s->cur]);
-    a.g_out = static_cast<T*>(s->g[s->cur ^ 1]);
-    a.dpsi_in = s->dpsi[s->cur];
-    a.dpsi_out = s->dpsi[s->cur ^ 1];
+    a.g_in = static_cast<const T*>(s->g[cur]);
+    a.g_out = static_cast<T*>(s->g[cur ^ 1]);
+    a.dpsi_in = s->dpsi[cur];
+    a.dpsi_out = s->dpsi[cur ^ 1];
     a.nx = p.nx;
     a.ny = p.ny;
     a.rows = s->launch.rows;
@@ -158,6 +138,15 @@ StepArgs<T> make_args(const lb_state* s)
     a.extra_tx = s->extra_tx;
     return a;
 }
+
+template StepArgs<float> state_args<float>(const lb_state*, int);
+template StepArgs<__half> state_args<__half>(const lb_state*, int);
+
+size_t elem_size(lb_precision p) { return p == LB_FP16_DELTA ? 2 : 4; }
+
+}  // namespace lbsc
+
+namespace {
 
 lb_status fail_cuda(lb_state* s)
 {
@@ -351,7 +340,10 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return bail(LB_ERR_CUDA);
     if (flag) return bail(LB_ERR_ARG);
-    s->rho_ref = p->rho_ref > 0.0 ? p->rho_ref : sum / (double)N;
+    // The reference density is rounded to FP32 once: the kernels add it in FP32,
+    // the deviations at init and the mass/field reconstructions use it in FP64,
+    // and all of them must mean the same number.
+    s->rho_ref = (double)(float)(p->rho_ref > 0.0 ? p->rho_ref : sum / (double)N);
     cudaError_t e;
     if (p->prec == LB_FP64)
         e = fp64_init(s->f64[0], rho_dev, p->nx, p->ny, s->stream);

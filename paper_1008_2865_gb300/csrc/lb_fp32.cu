@@ -80,8 +80,20 @@ __device__ __forceinline__ int next_row(int off, int nx, int N)
     return off == N ? 0 : off;
 }
 
+// Resident warps per SM the register budget is cut for: the plain omega = 1 step
+// fits 48 warps (40 registers) in CTAs of 128 threads or more, the other plain
+// steps 40 warps and the reduction step 32 warps, all without spills. The step
+// is bound by the latency of its global loads, so occupancy is throughput here.
+template <int BX, bool REDUCE, bool OM1>
+struct StepWarps {
+    static constexpr int value = REDUCE ? 32 : ((OM1 && BX >= 128) ? 48 : 40);
+};
+
+// One CTA's tile of the step: output columns [bx (BX-2), +BX-2) and output
+// rows [by rows, +rows). With REDUCE, v receives this thread's FP64 partial
+// sums {E_s, E_m, E_bulk, sum of rho - rho_ref} of state t over its sites.
 template <typename T, int BX, bool REDUCE, bool OM1>
-__global__ void __launch_bounds__(BX) k_step(const StepArgs<T> a)
+__device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, double v[4])
 {
     constexpr int W = BX + 4;
     __shared__ float win[8][W];              // dpsi(t) rows, slot = row & 7
@@ -91,8 +103,8 @@ __global__ void __launch_bounds__(BX) k_step(const StepArgs<T> a)
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
     const int N = (int)a.N;
-    const int x0 = blockIdx.x * (BX - 2);
-    const int y0 = blockIdx.y * a.rows;
+    const int x0 = bx * (BX - 2);
+    const int y0 = by * a.rows;
     const int y1 = min(y0 + a.rows, ny);
     const int txe = min(BX - 2, nx - x0);
     const bool out_col = tid >= 1 && tid <= txe;
@@ -151,18 +163,12 @@ __global__ void __launch_bounds__(BX) k_step(const StepArgs<T> a)
         float gs[9];
         const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
 
-        if (out_col && r >= y0 && r < y1) {
+        const bool out_site = out_col && r >= y0 && r < y1;
+        if (out_site) {
             T* o = a.g_out + (r * nx + xc);
 #pragma unroll
             for (int i = 0; i < 9; ++i) st_(o + i * N, gs[i]);
-            if (REDUCE) {
-                energy_site(rows, pc, a, es, em, eb);
-                ms += d;
-                if (((r - y0) & 15) == 15) {
-                    d_es += es; d_em += em; d_eb += eb; d_ms += ms;
-                    es = em = eb = ms = 0.f;
-                }
-            }
+            if (REDUCE) ms += d;
         }
 
         // ---- exchange post-collision values with the neighbouring columns
@@ -183,15 +189,91 @@ __global__ void __launch_bounds__(BX) k_step(const StepArgs<T> a)
         acc_0 = acc_p;
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fn[i];
+        if (REDUCE && out_site) {
+            // Sec. 5 energies of state t at (x, r); the dpsi rows r-2..r+2 stay in the
+            // ring until the next iteration overwrites slot (r+4) & 7
+            energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
+            if (((r - y0) & 15) == 15) {
+                d_es += es; d_em += em; d_eb += eb; d_ms += ms;
+                es = em = eb = ms = 0.f;
+            }
+        }
     }
 
     if (REDUCE) {
-        double v[4] = {d_es + es, d_em + em, d_eb + eb, d_ms + ms};
+        v[0] = d_es + es;
+        v[1] = d_em + em;
+        v[2] = d_eb + eb;
+        v[3] = d_ms + ms;
+    }
+}
+
+template <typename T, int BX, bool REDUCE, bool OM1>
+__global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / BX)
+    k_step(const StepArgs<T> a)
+{
+    double v[4];
+    step_tile<T, BX, REDUCE, OM1>(a, blockIdx.x, blockIdx.y, v);
+    if (REDUCE) {
         const unsigned int nb = gridDim.x * gridDim.y;
         if (last_block_total<BX>(v, a.partials, a.counter, nb)) {
             const double mass = (double)a.N * (double)a.rho_ref + v[3];
             write_trace_row(a.trace, a.trace_count, a.t, mass, v[0], v[1], v[2]);
         }
+    }
+}
+
+// ---------------------------------------------------------------- batches
+// Several lattices (replicas, each with its own size and couplings) advanced by
+// one launch: a persistent grid strides over a work list of tiles, each tile
+// = (replica, strip, row chunk) of that replica's own launch shape, and runs
+// exactly the per-tile code of k_step. The replica's arguments are staged in
+// shared memory once per tile. With REDUCE each tile's CTA partial (the same
+// block sum k_step forms) goes to tile_partials; k_batch_reduce then sums a
+// replica's partials in the order k_step's last CTA uses, so a replica's
+// fields and trace are bit-identical to running it alone with the same shape.
+template <typename T, int BX, bool REDUCE, bool OM1>
+__global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
+    k_step_batch(const StepArgs<T>* __restrict__ args, const int4* __restrict__ tiles, int ntiles,
+                 double* __restrict__ tile_partials)
+{
+    __shared__ StepArgs<T> sa;
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const int4 tl = tiles[k];                   // (replica, strip, chunk, -)
+        __syncthreads();                            // previous tile done with sa and smem rings
+        if (threadIdx.x == 0) sa = args[tl.x];
+        __syncthreads();
+        double v[4];
+        step_tile<T, BX, REDUCE, OM1>(sa, tl.y, tl.z, v);
+        if (REDUCE) {
+            block_sum4<BX>(v);
+            if (threadIdx.x == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tile_partials[4 * (size_t)k + q] = v[q];
+            }
+        }
+    }
+}
+
+// One CTA per replica: the replica's tile partials (tiles first .. first+n-1,
+// in the replica's own CTA order) summed like last_block_total, then one trace
+// row (t = rows already written x trace_every) into the replica's trace ring.
+template <int BX>
+__global__ void __launch_bounds__(BX)
+    k_batch_reduce(const double* __restrict__ tile_partials, const BatchRep* __restrict__ reps,
+                   int trace_every)
+{
+    const BatchRep r = reps[blockIdx.x];
+    double w[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = threadIdx.x; j < r.ntiles; j += BX) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[q] += tile_partials[4 * (size_t)(r.first_tile + j) + q];
+    }
+    block_sum4<BX>(w);
+    if (threadIdx.x == 0) {
+        const double mass = (double)r.N * r.rho_ref + w[3];
+        const long long t = (long long)(*r.trace_count) * trace_every;
+        write_trace_row(r.trace, r.trace_count, t, mass, w[0], w[1], w[2]);
     }
 }
 
@@ -217,7 +299,7 @@ __global__ void k_delta_init(T* __restrict__ g, float* __restrict__ dpsi,
             const long long src = (long long)wrapi(y + cy[i], ny) * nx + wrapi(x + cx[i], nx);
             st_(g + i * N + s, (float)(w[i] * (rho[src] - rho_ref)));
         }
-        dpsi[s] = (float)(cpsi * expm1(-(rho[s] - rho_ref) / rho0));
+        dpsi[s] = (float)cpsi * expm1f((float)(-(rho[s] - rho_ref) / rho0));
     }
 }
 
@@ -353,6 +435,52 @@ cudaError_t fp32_step(const StepArgs<float>& a, Fp32Launch L, bool reduce, cudaS
 cudaError_t fp16_step(const StepArgs<__half>& a, Fp32Launch L, bool reduce, cudaStream_t s)
 {
     return launch_step<__half>(a, L, reduce, s);
+}
+
+template <typename T, int BX>
+cudaError_t launch_batch_bx(const BatchLaunch<T>& b, bool reduce, cudaStream_t s)
+{
+    auto pick = [&](auto kern) -> cudaError_t {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BX, 0);
+        if (e != cudaSuccess) return e;
+        long long grid = (long long)per_sm * b.num_sms;
+        if (grid > b.ntiles) grid = b.ntiles;
+        if (grid < 1) grid = 1;
+        kern<<<(unsigned int)grid, BX, 0, s>>>(b.args, b.tiles, b.ntiles, b.tile_partials);
+        return cudaGetLastError();
+    };
+    cudaError_t e;
+    if (reduce)
+        e = b.om1 ? pick(k_step_batch<T, BX, true, true>) : pick(k_step_batch<T, BX, true, false>);
+    else
+        e = b.om1 ? pick(k_step_batch<T, BX, false, true>) : pick(k_step_batch<T, BX, false, false>);
+    if (e != cudaSuccess || !reduce) return e;
+    k_batch_reduce<BX><<<b.nreps, BX, 0, s>>>(b.tile_partials, b.reps, b.trace_every);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch(const BatchLaunch<T>& b, bool reduce, cudaStream_t s)
+{
+    switch (b.block_x) {
+    case 64: return launch_batch_bx<T, 64>(b, reduce, s);
+    case 96: return launch_batch_bx<T, 96>(b, reduce, s);
+    case 128: return launch_batch_bx<T, 128>(b, reduce, s);
+    case 192: return launch_batch_bx<T, 192>(b, reduce, s);
+    case 256: return launch_batch_bx<T, 256>(b, reduce, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t fp32_batch_step(const BatchLaunch<float>& b, bool reduce, cudaStream_t s)
+{
+    return launch_batch<float>(b, reduce, s);
+}
+
+cudaError_t fp16_batch_step(const BatchLaunch<__half>& b, bool reduce, cudaStream_t s)
+{
+    return launch_batch<__half>(b, reduce, s);
 }
 
 static int helper_grid(long long n)

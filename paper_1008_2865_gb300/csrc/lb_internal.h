@@ -59,6 +59,31 @@ struct Fp32Launch {
 int fp32_grid_blocks(int nx, int ny, Fp32Launch L);
 cudaError_t fp32_step(const StepArgs<float>& a, Fp32Launch L, bool reduce, cudaStream_t s);
 cudaError_t fp16_step(const StepArgs<__half>& a, Fp32Launch L, bool reduce, cudaStream_t s);
+// Batches (lb_fp32.cu kernels, lb_batch.cu host code): one launch advances many
+// replicas. tiles[k] = (replica, strip, chunk, 0), grouped by replica in each
+// replica's own CTA order; reps[r] locates replica r's tiles and its trace ring.
+struct BatchRep {
+    int first_tile, ntiles;
+    long long N;
+    double rho_ref;
+    double* trace;
+    int* trace_count;
+};
+template <typename T>
+struct BatchLaunch {
+    const StepArgs<T>* args;   // [nreps] arguments of this step's parity
+    const int4* tiles;
+    int ntiles;
+    double* tile_partials;     // [ntiles][4]
+    const BatchRep* reps;
+    int nreps;
+    int block_x;
+    bool om1;                  // every replica has omega == 1
+    int trace_every;
+    int num_sms;
+};
+cudaError_t fp32_batch_step(const BatchLaunch<float>& b, bool reduce, cudaStream_t s);
+cudaError_t fp16_batch_step(const BatchLaunch<__half>& b, bool reduce, cudaStream_t s);
 // bulk-copy pipelined step (lb_bulk.cu)
 bool bulk_supported(int nx, int ny, int elem_bytes, int block_x);
 int bulk_grid_blocks(int nx, int ny, int elem_bytes, Fp32Launch L);
@@ -98,4 +123,42 @@ cudaError_t fp64_fields(const double* f, int nx, int ny, double* rho, double* ux
                         cudaStream_t s);
 cudaError_t fp64_exp_cr(const double* x, double* y, long long n, cudaStream_t s);
 
+}  // namespace lbsc
+
+// The state behind the opaque lb_state* of the C ABI (lb_api.cu owns its
+// lifetime; lb_batch.cu drives several of them with one launch per step).
+struct lb_state {
+    lb_params p;
+    cudaStream_t stream = nullptr;
+    long long t = 0;
+    bool poisoned = false;
+    long long N = 0;
+    // FP32 / FP16 deviation storage
+    void* g[2] = {nullptr, nullptr};
+    float* dpsi[2] = {nullptr, nullptr};
+    int cur = 0;
+    double rho_ref = 0.0;
+    lbsc::Fp32Launch launch{128, 64, 0};
+    int* err = nullptr;            // set by a kernel whose bounded wait ran out
+    long long wait_cycles = 2000000000LL;
+    unsigned int extra_tx = 0;
+    // FP64 parity storage
+    double* f64[2] = {nullptr, nullptr};
+    double* psi64 = nullptr;
+    double* rho64 = nullptr;
+    // reductions, trace, scratch
+    double* partials = nullptr;
+    size_t partials_cap = 0;       // number of 4-double partials
+    unsigned int* counter = nullptr;
+    double* trace = nullptr;
+    int* trace_count = nullptr;
+    double* res = nullptr;         // 4 doubles of results
+    int* flag = nullptr;
+    double* field_tmp = nullptr;   // N doubles, allocated on the first host-destined lb_fields
+};
+
+namespace lbsc {
+template <typename T>
+StepArgs<T> state_args(const lb_state* s, int cur);   // arguments of a step from buffers `cur`
+size_t elem_size(lb_precision p);
 }  // namespace lbsc

@@ -105,7 +105,73 @@ def tune(nx, ny, prec="fp32", steps=20, device=0, save=True, G1=-5.0, G2=0.6):
     return best, table
 
 
-if __name__ == "__main__":
+def _batch_key(shapes, prec, device=0):
+    import hashlib
+    h = hashlib.sha1(repr(sorted(shapes)).encode()).hexdigest()[:12]
+    return f"{_gpu_name(device)}|batch:{len(shapes)}:{h}|{prec}"
+
+
+def lookup_batch(shapes, prec="fp32", device=0):
+    """Cached (block_x, rows_per_cta) for a batch of these lattice shapes, or None."""
+    rec = _load_cache().get(_batch_key(shapes, prec, device))
+    return tuple(rec["best"]) if rec else None
+
+
+def tune_batch(rho_list, G2_list, prec="fp32", steps=20, device=0, save=True, G1=-5.0):
+    """Time each tile shape for a batch (one launch per step over all replicas, graph
+    replay) and return ((block_x, rows), {shape: ms_per_step})."""
+    import torch
+
+    from . import Batch
+
+    stream = torch.cuda.current_stream(device)
+    shapes = [tuple(r.shape) for r in rho_list]
+    sites = sum(a * b for a, b in shapes)
+    table = {}
+    with Batch(rho_list, G1=G1, G2=list(G2_list), prec=prec, trace_every=10, device=device,
+               stream=stream.cuda_stream) as b:
+        for bx in BLOCK_X:
+            for rows in (16, 24, 32, 48, 64):
+                try:
+                    b.set_launch(bx, rows, 1)
+                except Exception:
+                    continue
+                b.step(10)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                b.step(steps)
+                e1.record(stream)
+                e1.synchronize()
+                table[(bx, rows)] = e0.elapsed_time(e1) / steps
+    best = min(table, key=table.get)
+    if save:
+        with _lock:
+            cache = _load_cache()
+            cache[_batch_key(shapes, prec, device)] = {
+                "best": list(best), "ms_per_step": table[best],
+                "mlups": sites / (table[best] / 1e3) / 1e6,
+                "candidates": {f"{b},{r}": round(v, 5) for (b, r), v in sorted(table.items())},
+            }
+            tmp = CACHE + f".tmp{os.getpid()}"
+            with open(tmp, "w") as fh:
+                json.dump(cache, fh, indent=1, sort_keys=True)
+            os.replace(tmp, CACHE)
+    return best, table
+
+
+if __name__ == "__main__" and len(sys.argv) > 1 and sys.argv[1] == "batch":
+    # the 96-replica G2 sweep: 32 each of 192^2, 384^2, 640^2
+    from . import inputs
+    sizes = [n for n in (192, 384, 640) for _ in range(32)]
+    g2 = inputs.g2_sweep(len(sizes), seed=100)
+    rhos = [inputs.noisy_density(n, n, 1000 + i, mean=0.7, amp=0.01, mode="rel")
+            for i, n in enumerate(sizes)]
+    best, table = tune_batch(rhos, g2)
+    for k in sorted(table, key=table.get)[:8]:
+        print(k, f"{table[k]:.4f} ms/step")
+    print("best", best)
+elif __name__ == "__main__":
     nx = int(sys.argv[1]) if len(sys.argv) > 1 else 8192
     ny = int(sys.argv[2]) if len(sys.argv) > 2 else nx
     prec = sys.argv[3] if len(sys.argv) > 3 else "fp32"

@@ -43,6 +43,29 @@ def test_library_exports_every_declared_symbol(lib):
             assert hasattr(lib, name)
 
 
+def _prototypes(header):
+    """{name: number of parameters} of the functions a header declares."""
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(lb_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_header(lib):
+    """Every function the binding declares passes as many arguments as the C prototype."""
+    protos = {}
+    for header in os.listdir(os.path.join(ROOT, "include")):
+        protos.update(_prototypes(header))
+    assert len(protos) >= 20
+    for name, nargs in protos.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, f"{name} has no argtypes in the binding"
+        assert len(fn.argtypes) == nargs, (name, len(fn.argtypes), nargs)
+
+
 def test_params_struct_layout_matches_header(lib):
     # the ctypes mirror must match the C layout: offsets of doubles after ints
     P = capi.lb_params

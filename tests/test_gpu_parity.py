@@ -237,13 +237,17 @@ def test_device_pointers_and_partial_fields():
         assert np.array_equal(only_ux, h_ux)
 
 
-def test_default_pipeline_choice():
+def test_pipeline_availability():
     with Lattice(inputs.noisy_density(512, 64, seed=1)) as lat:
-        assert lat.launch[2] == 1                  # aligned and wide: bulk-copy rings
+        assert lat.launch[2] == 0                  # default: register prefetch
+        lat.set_launch(128, 32, 1)                 # aligned and wide: rings allowed
+        assert lat.launch == (128, 32, 1)
     with Lattice(inputs.noisy_density(301, 64, seed=1)) as lat:
-        assert lat.launch[2] == 0                  # odd width: register prefetch
+        with pytest.raises(LBError):
+            lat.set_launch(128, 32, 1)             # odd width: no 16-byte row alignment
     with Lattice(inputs.noisy_density(516, 64, seed=1), prec="fp16_delta") as lat:
-        assert lat.launch[2] == 0                  # fp16 rows need 8-element alignment
+        with pytest.raises(LBError):
+            lat.set_launch(128, 32, 1)             # fp16 rows need 8-element alignment
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
@@ -252,7 +256,7 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     CUDA context keeps working for a fresh state."""
     rho0 = inputs.noisy_density(256, 48, seed=2)
     lat = Lattice(rho0, trace_every=0)
-    assert lat.launch[2] == 1
+    lat.set_launch(128, 16, 1)
     capi.lb_set_wait_limit(lat.handle, 2_000_000, 16)    # ~1 ms per wait
     lat.step(1)
     with pytest.raises(LBError) as ei:
