@@ -81,6 +81,11 @@ def _bind(lib):
     lib.orc_run.argtypes = [pp, dp, ctypes.c_long, ctypes.c_int, dp, dp, dp,
                             dp, ctypes.c_int, ip]
     lib.orc_run.restype = ctypes.c_int
+    lib.orc_objective.argtypes = [pp, dp, ctypes.c_long, dp, dp]
+    lib.orc_objective.restype = ctypes.c_double
+    lib.orc_gradient.argtypes = [pp, dp, ctypes.c_long, dp, dp, dp, dp]
+    lib.orc_gradient.restype = ctypes.c_int
+    lib.orc_adjoint_step.argtypes = [pp, dp, dp, dp, dp]
     return lib
 
 
@@ -241,3 +246,42 @@ def run(rho_init, steps, omega=1.0, G1=-5.0, G2=0.0, rho0=1.0, trace_every=0,
     if rc != 0:
         raise ValueError("oracle rejected the parameters or ran out of memory")
     return rho, ux, uy, trace[: count.value].copy()
+
+
+def objective(rho_init, rho_target, steps, omega=1.0, G1=-5.0, G2=0.0, rho0=1.0):
+    """(J, E) with J = E_s(T) + E_m(T) + sum (rho(T) - rho_target)^2."""
+    rho_init = np.ascontiguousarray(rho_init, dtype=np.float64)
+    tgt = np.ascontiguousarray(rho_target, dtype=np.float64)
+    ny, nx = rho_init.shape
+    E = ctypes.c_double(0.0)
+    P = _params(nx, ny, omega, G1, G2, rho0)
+    J = _load().orc_objective(ctypes.byref(P), _dp(rho_init), int(steps), _dp(tgt),
+                              ctypes.byref(E))
+    return float(J), float(E.value)
+
+
+def gradient(rho_init, rho_target, steps, omega=1.0, G1=-5.0, G2=0.0, rho0=1.0):
+    """(J, dJ/drho_init [ny, nx], (dJ/dG1, dJ/dG2)) by the reverse sweep."""
+    rho_init = np.ascontiguousarray(rho_init, dtype=np.float64)
+    tgt = np.ascontiguousarray(rho_target, dtype=np.float64)
+    ny, nx = rho_init.shape
+    g = np.empty((ny, nx))
+    gG = np.empty(2)
+    J = ctypes.c_double(0.0)
+    P = _params(nx, ny, omega, G1, G2, rho0)
+    if _load().orc_gradient(ctypes.byref(P), _dp(rho_init), int(steps), _dp(tgt),
+                            ctypes.byref(J), _dp(g), _dp(gG)) != 0:
+        raise ValueError("oracle rejected the parameters or ran out of memory")
+    return float(J.value), g, (float(gG[0]), float(gG[1]))
+
+
+def adjoint_step(f, lam_next, omega=1.0, G1=-5.0, G2=0.0, rho0=1.0):
+    """(lam, (gG1, gG2)): the transpose of one step's Jacobian at f applied to lam_next."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    ln = np.ascontiguousarray(lam_next, dtype=np.float64)
+    _, ny, nx = f.shape
+    lam = np.empty_like(f)
+    gG = np.empty(2)
+    P = _params(nx, ny, omega, G1, G2, rho0)
+    _load().orc_adjoint_step(ctypes.byref(P), _dp(f), _dp(ln), _dp(lam), _dp(gG))
+    return lam, (float(gG[0]), float(gG[1]))

@@ -359,3 +359,221 @@ int orc_run(const orc_params* P, const double* rho_init, long steps, int trace_e
     free(fa); free(fb); free(rho); free(psi);
     return 0;
 }
+
+/* ---- objective and its gradient (reverse mode) --------------------------- */
+/*
+ * J = E_s(T) + E_m(T) + sum_x (rho(x, T) - rho_target(x))^2: the pseudo-energy
+ * of Sec. 5 at the final state plus a squared misfit of the final density to
+ * a target field. The gradient with respect to the initial density, G1 and G2
+ * is the plain reverse sweep of the step above, written out by hand:
+ *   streaming   f_i(x + c_i, t+1) = f*_i(x)      ->  l*_i(x) = l_i(x + c_i, t+1)
+ *   collision   f*_i = (1 - om) f_i + om feq_i(rho, v),  v = (j + F/om) / rho
+ *               feq_i = w_i rho (1 + 3 c_i.v + 9/2 (c_i.v)^2 - 3/2 v.v)
+ *   force       F(x) = -psi(x) S(x),  S(x) = sum_c K_c c psi(x + c)
+ *   psi         psi(rho),  psi' = exp(-rho/rho0) / sqrt(rho0)
+ *   moments     rho = sum_i f_i, j = sum_i c_i f_i
+ *   start       f_i(x, 0) = w_i rho_init(x)
+ * The force's transpose gathers Q = psi F-bar over the same 24-link stencil
+ * (K_c = K_{-c}). All T+1 states are kept in memory (no checkpointing).
+ */
+
+/* sum_c K_c c psi(x + c) split into the D2Q9 (w) and E(8) (p) parts:
+ * S = G1 Sw + G2 Sp. */
+static void stencil_sums(const orc_params* P, const double* psi, long x, long y,
+                         double* Swx, double* Swy, double* Spx, double* Spy)
+{
+    double wx = 0.0, wy = 0.0, px = 0.0, py = 0.0;
+    for (int i = 1; i <= 8; ++i) {
+        const double pn = psi[site(P, x + CX[i], y + CY[i])];
+        wx += W[i] * pn * CX[i];
+        wy += W[i] * pn * CY[i];
+        px += PS[i] * pn * CX[i];
+        py += PS[i] * pn * CY[i];
+    }
+    for (int k = 0; k < 16; ++k) {
+        const double pn = psi[site(P, x + MCX[k], y + MCY[k])];
+        px += PM[k] * pn * MCX[k];
+        py += PM[k] * pn * MCY[k];
+    }
+    *Swx = wx; *Swy = wy; *Spx = px; *Spy = py;
+}
+
+/* Pseudo-energy of Sec. 5 at psi and its partial derivatives:
+ * dE/dpsi(y) = sum_{c incl. rest} K_c psi(y + c); dE/dG1, dE/dG2. */
+static double energy_and_derivatives(const orc_params* P, const double* psi, double* dEdpsi,
+                                     double* dEdG1, double* dEdG2)
+{
+    const long nx = P->nx, ny = P->ny;
+    const double p0 = ps_rest();
+    double E = 0.0, g1 = 0.0, g2 = 0.0;
+    for (long y = 0; y < ny; ++y)
+        for (long x = 0; x < nx; ++x) {
+            const double ps = psi[y * nx + x];
+            double sw = W[0] * ps, sp = p0 * ps;           /* rest link */
+            for (int i = 1; i <= 8; ++i) {
+                const double pn = psi[site(P, x + CX[i], y + CY[i])];
+                sw += W[i] * pn;
+                sp += PS[i] * pn;
+            }
+            for (int k = 0; k < 16; ++k) sp += PM[k] * psi[site(P, x + MCX[k], y + MCY[k])];
+            const double sk = P->G1 * sw + P->G2 * sp;      /* sum_c K_c psi(x + c) */
+            E += 0.5 * ps * sk;
+            g1 += 0.5 * ps * sw;
+            g2 += 0.5 * ps * sp;
+            dEdpsi[y * nx + x] = sk;
+        }
+    *dEdG1 = g1;
+    *dEdG2 = g2;
+    return E;
+}
+
+/* One reverse step: lam_t = (d f(t+1) / d f(t))^T lam_next at the state f_t;
+ * adds the explicit dependence of step t on G1, G2 to gG[0], gG[1]. */
+static void adjoint_step(const orc_params* P, const double* f, const double* lam_next,
+                         double* lam, double* gG)
+{
+    const long nx = P->nx, ny = P->ny, N = nx * ny;
+    const double om = P->omega;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* Qx = (double*)malloc(sizeof(double) * N);
+    double* Qy = (double*)malloc(sizeof(double) * N);
+    double* rbar = (double*)malloc(sizeof(double) * N);
+    double* jbx = (double*)malloc(sizeof(double) * N);
+    double* jby = (double*)malloc(sizeof(double) * N);
+    psi_field(P, f, rho, psi);
+    double g1 = 0.0, g2 = 0.0;
+    for (long y = 0; y < ny; ++y)
+        for (long x = 0; x < nx; ++x) {
+            const long s = y * nx + x;
+            double r, jx, jy, ls[9];
+            moments_at(f, N, s, &r, &jx, &jy);
+            for (int i = 0; i < 9; ++i) ls[i] = lam_next[i * N + site(P, x + CX[i], y + CY[i])];
+            double Swx, Swy, Spx, Spy;
+            stencil_sums(P, psi, x, y, &Swx, &Swy, &Spx, &Spy);
+            const double Sx = P->G1 * Swx + P->G2 * Spx, Sy = P->G1 * Swy + P->G2 * Spy;
+            const double ps = psi[s];
+            const double Fx = -ps * Sx, Fy = -ps * Sy;
+            const double vx = (jx + Fx / om) / r, vy = (jy + Fy / om) / r;
+            const double usq = vx * vx + vy * vy;
+            double rb = 0.0, vbx = 0.0, vby = 0.0;
+            for (int i = 0; i < 9; ++i) {
+                const double cu = CX[i] * vx + CY[i] * vy;
+                const double feq = W[i] * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                rb += om * ls[i] * feq / r;                           /* d feq / d rho */
+                vbx += om * ls[i] * W[i] * r * (3.0 * CX[i] + 9.0 * cu * CX[i] - 3.0 * vx);
+                vby += om * ls[i] * W[i] * r * (3.0 * CY[i] + 9.0 * cu * CY[i] - 3.0 * vy);
+            }
+            /* v = (j + F/om) / rho */
+            jbx[s] = vbx / r;
+            jby[s] = vby / r;
+            const double Fbx = vbx / (om * r), Fby = vby / (om * r);
+            rb -= (vbx * vx + vby * vy) / r;
+            /* F = -psi S: the leading psi(x) and the couplings */
+            const double dpsi = exp_cr(-r / P->rho0) / sqrt(P->rho0);
+            rbar[s] = rb + dpsi * (-(Fbx * Sx + Fby * Sy));
+            Qx[s] = ps * Fbx;
+            Qy[s] = ps * Fby;
+            g1 += -ps * (Fbx * Swx + Fby * Swy);
+            g2 += -ps * (Fbx * Spx + Fby * Spy);
+        }
+    for (long y = 0; y < ny; ++y)
+        for (long x = 0; x < nx; ++x) {
+            const long s = y * nx + x;
+            /* psi(y) inside the neighbours' forces: sum_c K_c c . Q(y + c) */
+            double pb = 0.0;
+            for (int i = 1; i <= 8; ++i) {
+                const long n = site(P, x + CX[i], y + CY[i]);
+                const double K = P->G1 * W[i] + P->G2 * PS[i];
+                pb += K * (CX[i] * Qx[n] + CY[i] * Qy[n]);
+            }
+            for (int k = 0; k < 16; ++k) {
+                const long n = site(P, x + MCX[k], y + MCY[k]);
+                pb += P->G2 * PM[k] * (MCX[k] * Qx[n] + MCY[k] * Qy[n]);
+            }
+            const double dpsi = exp_cr(-rho[s] / P->rho0) / sqrt(P->rho0);
+            const double rb = rbar[s] + dpsi * pb;
+            for (int i = 0; i < 9; ++i) {
+                const double li = lam_next[i * N + site(P, x + CX[i], y + CY[i])];
+                lam[i * N + s] = (1.0 - om) * li + rb + CX[i] * jbx[s] + CY[i] * jby[s];
+            }
+        }
+    gG[0] += g1;
+    gG[1] += g2;
+    free(rho); free(psi); free(Qx); free(Qy); free(rbar); free(jbx); free(jby);
+}
+
+double orc_objective(const orc_params* P, const double* rho_init, long steps,
+                     const double* rho_target, double* E_out)
+{
+    if (!params_ok(P) || steps < 0) return NAN;
+    const long N = (long)P->nx * P->ny;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* d = (double*)malloc(sizeof(double) * N);
+    if (orc_run(P, rho_init, steps, 0, rho, NULL, NULL, NULL, 0, NULL) != 0) return NAN;
+    orc_psi(N, rho, P->rho0, psi);
+    double g1, g2;
+    const double E = energy_and_derivatives(P, psi, d, &g1, &g2);
+    double mis = 0.0;
+    for (long s = 0; s < N; ++s) mis += (rho[s] - rho_target[s]) * (rho[s] - rho_target[s]);
+    if (E_out) *E_out = E;
+    free(rho); free(psi); free(d);
+    return E + mis;
+}
+
+int orc_gradient(const orc_params* P, const double* rho_init, long steps,
+                 const double* rho_target, double* J, double* grad_rho, double* grad_G)
+{
+    if (!params_ok(P) || steps < 0) return -1;
+    const long N = (long)P->nx * P->ny;
+    double* f = (double*)malloc(sizeof(double) * 9 * N * (size_t)(steps + 1));
+    double* la = (double*)malloc(sizeof(double) * 9 * N);
+    double* lb = (double*)malloc(sizeof(double) * 9 * N);
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* psi = (double*)malloc(sizeof(double) * N);
+    double* dEdpsi = (double*)malloc(sizeof(double) * N);
+    if (!f || !la || !lb || !rho || !psi || !dEdpsi) {
+        free(f); free(la); free(lb); free(rho); free(psi); free(dEdpsi);
+        return -1;
+    }
+    orc_init(P, rho_init, f);
+    for (long t = 0; t < steps; ++t) orc_step(P, f + 9 * N * t, f + 9 * N * (t + 1));
+    const double* fT = f + 9 * N * steps;
+    psi_field(P, fT, rho, psi);
+    double gE1, gE2;
+    const double E = energy_and_derivatives(P, psi, dEdpsi, &gE1, &gE2);
+    double mis = 0.0;
+    for (long s = 0; s < N; ++s) mis += (rho[s] - rho_target[s]) * (rho[s] - rho_target[s]);
+    *J = E + mis;
+    /* terminal adjoint: dJ/df_i(y, T) = psi'(rho) dE/dpsi + 2 (rho - rho_target) */
+    for (long s = 0; s < N; ++s) {
+        const double v = exp_cr(-rho[s] / P->rho0) / sqrt(P->rho0) * dEdpsi[s] +
+                         2.0 * (rho[s] - rho_target[s]);
+        for (int i = 0; i < 9; ++i) la[i * N + s] = v;
+    }
+    grad_G[0] = gE1;
+    grad_G[1] = gE2;
+    for (long t = steps - 1; t >= 0; --t) {
+        adjoint_step(P, f + 9 * N * t, la, lb, grad_G);
+        double* tmp = la; la = lb; lb = tmp;
+    }
+    /* f_i(x, 0) = w_i rho_init(x) */
+    for (long s = 0; s < N; ++s) {
+        double g = 0.0;
+        for (int i = 0; i < 9; ++i) g += W[i] * la[i * N + s];
+        grad_rho[s] = g;
+    }
+    free(f); free(la); free(lb); free(rho); free(psi); free(dEdpsi);
+    return 0;
+}
+
+/* One reverse step on its own (for the dot-product identity): lam = J_step^T lam_next
+ * at state f; gG (2 doubles) receives the explicit G1, G2 terms. */
+void orc_adjoint_step(const orc_params* P, const double* f, const double* lam_next, double* lam,
+                      double* gG)
+{
+    gG[0] = 0.0;
+    gG[1] = 0.0;
+    adjoint_step(P, f, lam_next, lam, gG);
+}

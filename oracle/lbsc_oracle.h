@@ -67,6 +67,22 @@ int orc_run(const orc_params* P, const double* rho_init, long steps, int trace_e
             double* rho, double* ux, double* uy,
             double* trace, int trace_cap, int* trace_count);
 
+/* J = E_s(T) + E_m(T) + sum_x (rho(x, T) - rho_target(x))^2 after `steps`
+ * steps from f = w rho_init (the energy is also returned in *E if non-NULL).
+ * Returns NaN on bad arguments. */
+double orc_objective(const orc_params* P, const double* rho_init, long steps,
+                     const double* rho_target, double* E);
+
+/* J and its gradient with respect to rho_init (N values) and (G1, G2), by a
+ * hand-written reverse sweep over all stored states. Returns 0 or -1. */
+int orc_gradient(const orc_params* P, const double* rho_init, long steps,
+                 const double* rho_target, double* J, double* grad_rho, double* grad_G);
+
+/* The transpose of one step's Jacobian at populations f applied to lam_next
+ * (both [9][ny][nx]); gG receives the step's explicit d/dG1, d/dG2 terms. */
+void orc_adjoint_step(const orc_params* P, const double* f, const double* lam_next, double* lam,
+                      double* gG);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,14 @@ MUTANTS = {
     "energy rest term": [("double ss = (P->G1 * W[0] + P->G2 * p0) * ps;", "double ss = 0.0 * ps;")],
     "energy belt-2 coupling": [("sm += P->G2 * PM[k]", "sm += P->G1 * PM[k]")],
     "energy half factor": [("em += 0.5 * ps * sm;", "em += ps * sm;")],
+    "adjoint: velocity term of the collision": [("rb -= (vbx * vx + vby * vy) / r;",
+                                                 "rb += (vbx * vx + vby * vy) / r;")],
+    "adjoint: force transpose gather dropped": [("pb += K * (CX[i] * Qx[n] + CY[i] * Qy[n]);",
+                                                 "pb += 0.0 * K;")],
+    "adjoint: reverse streaming direction": [("ls[i] = lam_next[i * N + site(P, x + CX[i], y + CY[i])];",
+                                              "ls[i] = lam_next[i * N + site(P, x - CX[i], y - CY[i])];")],
+    "adjoint: energy derivative factor": [("E += 0.5 * ps * sk;", "E += 0.5 * ps * sk + 0.0;"),
+                                          ("dEdpsi[y * nx + x] = sk;", "dEdpsi[y * nx + x] = 0.5 * sk;")],
     "diagonal weight": [("1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};",
                          "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 35.0};")],
 }
@@ -61,6 +69,9 @@ def _pin_calls(table1, d2q9, constants):
     for args in [(-5.0, 0.6, 1.0, (2, 1)), (-3.0, 0.4, 1.3, (3, 3))]:
         yield lambda args=args: pins.test_linear_mode_growth(table1, d2q9, *args)
     yield lambda: pins.test_brute_force_step_5x5(table1, d2q9)
+    import test_oracle_adjoint as adj
+    yield lambda: adj.test_reverse_step_is_the_transpose_of_the_step()
+    yield lambda: adj.test_gradient_matches_central_differences(0.5, 1.0, 10)
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
