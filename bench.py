@@ -187,6 +187,48 @@ def run_batched(steps, warmup, stream, dev):
             "launches_per_step": "1 (+1 per-replica reduction every 10 steps)"}
 
 
+def run_adjoint(stream, dev, T=2000, n=512):
+    """The adjoint workload: 512^2 periodic FP32, G1 = -5, G2 = 0.5, T = 2000 steps with
+    ceil(sqrt(T)) checkpointing; J = pseudo-energy at T + misfit to a seeded target.
+    Time of lb_adjoint (forward with checkpoints + recomputation + reverse sweep, its
+    working memory included) against T plain steps of the same lattice."""
+    import math
+
+    import torch
+
+    from paper_1008_2865_gb300 import Lattice, inputs
+    r0 = inputs.noisy_density(n, n, 11, mean=0.7, amp=0.01, mode="rel")
+    tgt = torch.from_numpy(inputs.noisy_density(n, n, 12, mean=0.7, amp=0.01, mode="rel")).cuda()
+    grad = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    res = {}
+    for rep in range(2):            # the first pass warms up allocations and module loads
+        with Lattice(r0, G1=G1, G2=0.5, trace_every=0, device=dev, stream=stream.cuda_stream) as lat:
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            lat.step(T)
+            e1.record(stream)
+            e1.synchronize()
+            res["forward_ms"] = e0.elapsed_time(e1)
+        with Lattice(r0, G1=G1, G2=0.5, trace_every=0, device=dev, stream=stream.cuda_stream) as lat:
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            J, _, gG = lat.adjoint(T, tgt, grad_rho=grad)
+            e1.record(stream)
+            e1.synchronize()
+            res["adjoint_ms"] = e0.elapsed_time(e1)
+    return {"workload": f"{n}x{n} periodic FP32 (FP64 gradient accumulation), G1=-5, G2=0.5, "
+                        f"T={T}, checkpoint every {math.ceil(math.sqrt(T))} steps; "
+                        "J = E_s(T) + E_m(T) + sum (rho(T) - rho*)^2, rho* seeded (seed 12)",
+            "forward_ms": res["forward_ms"], "adjoint_ms": res["adjoint_ms"],
+            "adjoint_over_forward": res["adjoint_ms"] / res["forward_ms"],
+            "J": J, "dJ_dG1": gG[0], "dJ_dG2": gG[1],
+            "includes": "forward with checkpoints, per-segment recomputation, reverse sweep "
+                        "(2 kernels per step), gradient w.r.t. rho_init, G1, G2"}
+
+
 def cpu_baseline(seconds=12.0):
     """Oracle MLUPS on the host cores: a 512x512 lattice of the workload's parameters."""
     import oracle
@@ -334,6 +376,7 @@ def run_ours(args):
     e2e_value = N * args.steps * ws / dt_e2e / 1e6
 
     batched = run_batched(args.steps, args.warmup, stream, dev) if not args.skip_batch else None
+    adjoint = run_adjoint(stream, dev) if not args.skip_batch else None
 
     out = None
     if rank == 0:
@@ -367,6 +410,7 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "clocks": clocks,
             "batched": batched,
+            "adjoint": adjoint,
         }
     if ws > 1:
         import torch.distributed as dist
@@ -390,7 +434,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true",
                     help="time the device-resident steps only and print a short line")
     ap.add_argument("--skip-batch", action="store_true",
-                    help="leave out the batched 96-replica sweep")
+                    help="leave out the batched 96-replica sweep and the adjoint workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

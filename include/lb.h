@@ -145,6 +145,26 @@ lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta, int pipeline
  * Errors: LB_ERR_ARG (NULL, cycles <= 0). */
 lb_status lb_set_wait_limit(lb_state* s, long long cycles, unsigned int extra_expect_bytes);
 
+/* Gradient of J = E_s(T) + E_m(T) + sum_x (rho(x, T) - rho_target(x))^2 — the
+ * Sec. 5 pseudo-energy of the state after `steps` steps plus the squared misfit
+ * of its density to a target field — with respect to the initial density
+ * field and the couplings G1, G2 of Eq. FORCE, by a hand-written reverse sweep
+ * of the step (FP32 state and adjoint, FP64 accumulation of J and of the G1,
+ * G2 gradients) with checkpointing: the forward run stores its state every
+ * checkpoint_every steps (0 picks ceil(sqrt(steps))), and each segment is
+ * recomputed from its checkpoint before the reverse sweep crosses it.
+ *   s             an LB_FP32 state at t = 0 (fresh from lb_init); on return it
+ *                 holds the state at t = steps (trace rows as from lb_step)
+ *   rho_target    N doubles, host or device
+ *   J             host double: the objective
+ *   grad_rho      N doubles, host or device: dJ/drho_init(x)
+ *   grad_G        host doubles {dJ/dG1, dJ/dG2}
+ * Working memory (about 40 N (steps/C + C) bytes) is allocated for the call.
+ * Errors: LB_ERR_ARG, LB_ERR_STATE (not FP32, t != 0, poisoned), LB_ERR_OOM,
+ * LB_ERR_CUDA, LB_ERR_NONFINITE. */
+lb_status lb_adjoint(lb_state* s, long steps, const double* rho_target, int checkpoint_every,
+                     double* J, double* grad_rho, double* grad_G);
+
 /* ---- Batches: many independent lattices advanced by one launch per step ----
  * A batch holds `count` replicas (each with its own size, couplings, omega,
  * rho_ref and initial density; all with the same prec — LB_FP32 or

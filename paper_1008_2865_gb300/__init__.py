@@ -13,6 +13,7 @@ from . import capi, inputs  # noqa: F401
 from .capi import (lb_batch_count, lb_batch_destroy, lb_batch_energy, lb_batch_fields,  # noqa: F401
                    lb_batch_get_launch, lb_batch_init, lb_batch_set_launch, lb_batch_step,
                    lb_batch_time, lb_batch_trace)
+from .capi import lb_adjoint  # noqa: F401
 from .capi import (LBError, lb_destroy, lb_energy, lb_fields, lb_get_launch,  # noqa: F401
                    lb_init, lb_set_launch, lb_set_wait_limit, lb_status_str, lb_step, lb_time,
                    lb_trace, make_params)
@@ -58,6 +59,11 @@ class Lattice:
             return rho, ux, uy
         lb_fields(self.handle, rho, ux, uy)
         return rho, ux, uy
+
+    def adjoint(self, steps: int, rho_target, checkpoint_every: int = 0, grad_rho=None):
+        """(J, dJ/drho_init, (dJ/dG1, dJ/dG2)) of J = E_s(T) + E_m(T) + sum (rho(T) - rho*)^2
+        over `steps` steps from this (fresh, FP32) state; leaves the state at t = steps."""
+        return lb_adjoint(self.handle, steps, rho_target, checkpoint_every, grad_rho)
 
     @property
     def launch(self):

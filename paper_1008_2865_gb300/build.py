@@ -25,6 +25,7 @@ UNITS = {
     "lb_fp32.cu": [],
     "lb_bulk.cu": [],
     "lb_batch.cu": [],
+    "lb_adjoint.cu": [],
     "lb_fp64.cu": ["--fmad=false"],
     "lb_noalloc.cu": [],
 }

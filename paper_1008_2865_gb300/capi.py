@@ -105,6 +105,8 @@ def load(build_if_missing: bool = False):
             lib.lb_batch_time.restype = ctypes.c_long
             lib.lb_batch_destroy.argtypes = [vp]
             lib.lb_batch_destroy.restype = None
+            lib.lb_adjoint.argtypes = [vp, ctypes.c_long, vp, ctypes.c_int, dp, vp, dp]
+            lib.lb_adjoint.restype = ctypes.c_int
             lib.lb_energy_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_double, ctypes.c_double, vp, vp]
             lib.lb_energy_noalloc.restype = ctypes.c_int
@@ -215,6 +217,23 @@ def lb_energy_noalloc(psi, rho, nx: int, ny: int, G1: float, G2: float, out=None
                                   _ptr(out), ctypes.c_void_p(stream or None))
     _check(st, "lb_energy_noalloc")
     return tuple(float(v) for v in out) if host else out
+
+
+def lb_adjoint(h: int, steps: int, rho_target, checkpoint_every: int = 0, grad_rho=None):
+    """(J, grad_rho, (dJ/dG1, dJ/dG2)) for a fresh FP32 state; grad_rho may be a
+    caller array/tensor (host or device) or None for a new NumPy array."""
+    if isinstance(rho_target, np.ndarray):
+        rho_target = np.ascontiguousarray(rho_target, dtype=np.float64)
+    J = ctypes.c_double(0.0)
+    gG = (ctypes.c_double * 2)()
+    out = grad_rho
+    if out is None:
+        shape = getattr(rho_target, "shape", None)
+        out = np.empty(shape if shape is not None else (0,))
+    _check(load().lb_adjoint(ctypes.c_void_p(h), int(steps), _ptr(rho_target),
+                             int(checkpoint_every), ctypes.byref(J), _ptr(out), gG),
+           "lb_adjoint")
+    return float(J.value), out, (float(gG[0]), float(gG[1]))
 
 
 def lb_batch_init(params_list, rho_list, stream: int = 0) -> int:

@@ -1,0 +1,425 @@
+// lb_adjoint.cu — lb_adjoint: the gradient of
+//   J = E_s(T) + E_m(T) + sum_x (rho(x, T) - rho*(x))^2
+// (Sec. 5 pseudo-energy of the final state plus a squared misfit to a target
+// density) with respect to the initial density field and the couplings G1, G2
+// of Eq. FORCE, for an FP32 state, by a hand-written reverse sweep of the
+// fused step with sqrt(T) checkpointing.
+//
+// Forward (Eqs. 1-4, Eq. FORCE):  rho, j = moments of f;  psi(rho);
+//   F = -psi(x) S(x), S = sum_c K_c c psi(x+c);  v = (j + F/omega)/rho;
+//   f*_i = (1-omega) f_i + omega feq_i(rho, v);  f_i(x + c_i, t+1) = f*_i(x).
+// Reverse, with l' = dJ/df(t+1) and l* the streamed-back adjoint
+// l*_i(x) = l'_i(x + c_i):
+//   pass A (per site x):
+//     rho-bar = omega sum_i l*_i feq_i / rho - (v-bar . v) / rho
+//     v-bar   = omega rho sum_i l*_i w_i (3 c_i + 9 (c_i.v) c_i - 3 v)
+//     j-bar   = v-bar / rho,  F-bar = v-bar / (omega rho)
+//     psi-bar(x) gets -F-bar . S (the leading psi(x) of F(x)); Q = psi F-bar
+//     dJ/dG1 += -psi F-bar . S_w,  dJ/dG2 += -psi F-bar . S_p  (S = G1 S_w + G2 S_p)
+//   pass B (per site y): psi-bar(y) += sum_c K_c c . Q(y + c) (the transpose of the
+//     force stencil; K_c = K_{-c}); rho-bar += psi'(rho) psi-bar;
+//     l_i(y) = (1 - omega) l*_i(y) + rho-bar(y) + c_i . j-bar(y).
+// Terminal: l_i(y, T) = psi'(rho) sum_{c incl. rest} K_c psi(y+c) + 2 (rho - rho*).
+// Start: dJ/drho_init(x) = sum_i w_i l_i(x, 0).
+// The state and the adjoint are FP32; J and the G1, G2 gradients accumulate
+// in FP64 (per-thread, then deterministic CTA and grid sums).
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "lb_device.cuh"
+
+using namespace lbsc;
+using namespace lbsc::dev;
+
+namespace {
+
+constexpr int kAdjThreads = 256;
+
+__device__ __forceinline__ int wrp(int a, int n)
+{
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+// The 5 x 5 neighbourhood of a periodic FP32 field around (x, y): v[k][m] =
+// field(x + m - 2, y + k - 2).
+__device__ __forceinline__ void gather5(const float* __restrict__ fld, int x, int y, int nx,
+                                        int ny, float v[5][5])
+{
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float* row = fld + (long long)wrp(y + k - 2, ny) * nx;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) v[k][m] = __ldg(row + wrp(x + m - 2, nx));
+    }
+}
+
+// Pulled deviations f_i(x, y) - w_i rho_ref from post-collision deviations g*.
+__device__ __forceinline__ void pull_site(const float* __restrict__ g, int N, int x, int y, int nx,
+                                          int ny, float f[9])
+{
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int om = (y == 0 ? ny - 1 : y - 1) * nx, oc = y * nx, op = (y == ny - 1 ? 0 : y + 1) * nx;
+    f[0] = __ldg(g + oc + x);
+    f[1] = __ldg(g + N + oc + xm);
+    f[2] = __ldg(g + 2 * N + om + x);
+    f[3] = __ldg(g + 3 * N + oc + xp);
+    f[4] = __ldg(g + 4 * N + op + x);
+    f[5] = __ldg(g + 5 * N + om + xm);
+    f[6] = __ldg(g + 6 * N + om + xp);
+    f[7] = __ldg(g + 7 * N + op + xp);
+    f[8] = __ldg(g + 8 * N + op + xm);
+}
+
+__constant__ int ACX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int ACY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+struct AdjArgs {
+    StepArgs<float> a;        // couplings, weights, rho_ref, psi_ref, omega of the state
+    StepArgs<float> aw;       // couplings replaced by the D2Q9 weights (S_w)
+    StepArgs<float> ap;       // couplings replaced by the E(8) weights (S_p)
+    float G1, G2;
+    float sqrt_rho0;
+    const float* g;           // g*(t-1): pull gives f(t)
+    const float* dpsi;        // dpsi(t)
+    const float* lam_next;    // [9][N] dJ/df(t+1)
+    float* lam;               // [9][N] dJ/df(t)
+    float* Qx;
+    float* Qy;
+    float* jbx;
+    float* jby;
+    float* rbar;
+    float* dpsidrho;
+    const double* rho_target; // terminal kernel
+    double* partials;
+    unsigned int* counter;
+    double* acc;              // [4] FP64 accumulators
+};
+
+template <int NT>
+__device__ void accumulate_grid(double v[4], const AdjArgs& A)
+{
+    if (last_block_total<NT>(v, A.partials, A.counter, gridDim.x)) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) A.acc[k] += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A)
+{
+    const StepArgs<float>& a = A.a;
+    const int nx = a.nx, ny = a.ny, N = (int)a.N;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};   // E, misfit, dE/dG1, dE/dG2
+    for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
+        const int y = s / nx, x = s % nx;
+        float f[9];
+        pull_site(A.g, N, x, y, nx, ny, f);
+        const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+        const float rho = a.rho_ref + d;
+        float p[5][5];
+        gather5(A.dpsi, x, y, nx, ny, p);
+        const float pr = a.psi_ref;
+        const float pc = pr + p[2][2];
+        // class sums of psi (not deviations) around the site
+        const float S1 = fmaf(4.f, pr, (p[2][3] + p[2][1]) + (p[3][2] + p[1][2]));
+        const float S2 = fmaf(4.f, pr, (p[3][3] + p[3][1]) + (p[1][3] + p[1][1]));
+        const float S4 = fmaf(4.f, pr, (p[2][4] + p[2][0]) + (p[4][2] + p[0][2]));
+        const float S5 = fmaf(8.f, pr, ((p[3][4] + p[3][0]) + (p[1][4] + p[1][0])) +
+                                           ((p[4][3] + p[4][1]) + (p[0][3] + p[0][1])));
+        const float S8 = fmaf(4.f, pr, (p[4][4] + p[4][0]) + (p[0][4] + p[0][0]));
+        const float dEdpsi = a.K0 * pc + a.K1 * S1 + a.K2 * S2 + a.K4 * S4 + a.K5 * S5 + a.K8 * S8;
+        const float sw = A.aw.K0 * pc + A.aw.K1 * S1 + A.aw.K2 * S2;
+        const float sp = A.ap.K0 * pc + A.ap.K1 * S1 + A.ap.K2 * S2 + A.ap.K4 * S4 +
+                         A.ap.K5 * S5 + A.ap.K8 * S8;
+        const float dpr = __expf(-rho * a.inv_rho0) / A.sqrt_rho0;
+        const double mis = (double)rho - A.rho_target[s];
+        const float lam = dpr * dEdpsi + (float)(2.0 * mis);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) A.lam[i * N + s] = lam;
+        v[0] += 0.5 * (double)pc * dEdpsi;
+        v[1] += mis * mis;
+        v[2] += 0.5 * (double)pc * sw;
+        v[3] += 0.5 * (double)pc * sp;
+    }
+    accumulate_grid<kAdjThreads>(v, A);
+}
+
+__global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
+{
+    const StepArgs<float>& a = A.a;
+    const int nx = a.nx, ny = a.ny, N = (int)a.N;
+    const float om = a.omega;
+    const float w[9] = {a.w0, a.w1, a.w1, a.w1, a.w1, a.w2, a.w2, a.w2, a.w2};
+    double v[4] = {0.0, 0.0, 0.0, 0.0};   // dJ/dG1, dJ/dG2
+    for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
+        const int y = s / nx, x = s % nx;
+        float f[9];
+        pull_site(A.g, N, x, y, nx, ny, f);
+        const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+        const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+        const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+        const float rho = a.rho_ref + d;
+        float p[5][5];
+        gather5(A.dpsi, x, y, nx, ny, p);
+        const float* rows[5] = {&p[0][2], &p[1][2], &p[2][2], &p[3][2], &p[4][2]};
+        float Swx, Swy, Spx, Spy;
+        force_sums(rows, A.aw, Swx, Swy);
+        force_sums(rows, A.ap, Spx, Spy);
+        const float Sx = A.G1 * Swx + A.G2 * Spx, Sy = A.G1 * Swy + A.G2 * Spy;
+        const float pc = a.psi_ref + p[2][2];
+        const float Fx = -pc * Sx, Fy = -pc * Sy;
+        const float inv = 1.f / rho;
+        const float vx = fmaf(Fx, a.inv_omega, jx) * inv, vy = fmaf(Fy, a.inv_omega, jy) * inv;
+        const float usq = vx * vx + vy * vy;
+        float rb = 0.f, vbx = 0.f, vby = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int xi = wrp(x + ACX[i], nx), yi = wrp(y + ACY[i], ny);
+            const float ls = __ldg(A.lam_next + i * N + yi * nx + xi);   // streamed back
+            const float cu = ACX[i] * vx + ACY[i] * vy;
+            const float feq = w[i] * rho * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * usq);
+            rb += om * ls * feq * inv;
+            const float k = om * ls * w[i] * rho;
+            vbx += k * (3.f * ACX[i] + 9.f * cu * ACX[i] - 3.f * vx);
+            vby += k * (3.f * ACY[i] + 9.f * cu * ACY[i] - 3.f * vy);
+        }
+        const float Fbx = vbx * inv / om, Fby = vby * inv / om;
+        rb -= (vbx * vx + vby * vy) * inv;
+        const float dpr = __expf(-rho * a.inv_rho0) / A.sqrt_rho0;
+        A.jbx[s] = vbx * inv;
+        A.jby[s] = vby * inv;
+        A.rbar[s] = rb + dpr * (-(Fbx * Sx + Fby * Sy));
+        A.dpsidrho[s] = dpr;
+        A.Qx[s] = pc * Fbx;
+        A.Qy[s] = pc * Fby;
+        v[0] += -(double)pc * (double)(Fbx * Swx + Fby * Swy);
+        v[1] += -(double)pc * (double)(Fbx * Spx + Fby * Spy);
+    }
+    accumulate_grid<kAdjThreads>(v, A);
+}
+
+__global__ void __launch_bounds__(kAdjThreads) k_adj_pass_b(const AdjArgs A)
+{
+    const StepArgs<float>& a = A.a;
+    const int nx = a.nx, ny = a.ny, N = (int)a.N;
+    const float omc = a.omc;
+    for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
+        const int y = s / nx, x = s % nx;
+        // sum_c K_c c . Q(y + c): the x part is the force stencil of Qx, the y part of Qy
+        float q[5][5];
+        const float* rows[5] = {&q[0][2], &q[1][2], &q[2][2], &q[3][2], &q[4][2]};
+        float sx, sy, tx, ty;
+        gather5(A.Qx, x, y, nx, ny, q);
+        force_sums(rows, a, sx, sy);
+        gather5(A.Qy, x, y, nx, ny, q);
+        force_sums(rows, a, tx, ty);
+        const float rb = A.rbar[s] + A.dpsidrho[s] * (sx + ty);
+        const float jbx = A.jbx[s], jby = A.jby[s];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int xi = wrp(x + ACX[i], nx), yi = wrp(y + ACY[i], ny);
+            const float ls = __ldg(A.lam_next + i * N + yi * nx + xi);
+            A.lam[i * N + s] = fmaf(omc, ls, rb + ACX[i] * jbx + ACY[i] * jby);
+        }
+    }
+}
+
+__global__ void k_adj_grad_init(const float* __restrict__ lam, int N, float w0, float w1, float w2,
+                                double* __restrict__ out)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const double g = (double)w0 * lam[s] +
+                         (double)w1 * (((double)lam[N + s] + lam[2 * N + s]) +
+                                       ((double)lam[3 * N + s] + lam[4 * N + s])) +
+                         (double)w2 * (((double)lam[5 * N + s] + lam[6 * N + s]) +
+                                       ((double)lam[7 * N + s] + lam[8 * N + s]));
+        out[s] = g;
+    }
+}
+
+int adj_grid(long long n)
+{
+    long long b = (n + kAdjThreads - 1) / kAdjThreads;
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)(b < 1 ? 1 : b);
+}
+
+bool dev_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+StepArgs<float> with_weights(StepArgs<float> a, bool e8)
+{
+    // the same stencil code with unit couplings: the D2Q9 weights (belt 1 and
+    // rest) or the E(8) weights (both belts and rest, Table 1, Eq. weights_1)
+    if (!e8) {
+        a.K0 = 4.f / 9.f; a.K1 = 1.f / 9.f; a.K2 = 1.f / 36.f; a.K4 = 0.f; a.K5 = 0.f; a.K8 = 0.f;
+    } else {
+        a.K0 = (float)(247.0 / 420.0); a.K1 = 4.f / 63.f; a.K2 = 4.f / 135.f;
+        a.K4 = 1.f / 180.f; a.K5 = 2.f / 945.f; a.K8 = 1.f / 15120.f;
+    }
+    return a;
+}
+
+}  // namespace
+
+extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_target,
+                                int checkpoint_every, double* J_out, double* grad_rho,
+                                double* grad_G)
+{
+    if (!s || steps < 0 || !rho_target || !J_out || !grad_rho || !grad_G || checkpoint_every < 0)
+        return LB_ERR_ARG;
+    if (s->poisoned) return LB_ERR_STATE;
+    if (s->p.prec != LB_FP32 || s->t != 0) return LB_ERR_STATE;
+    if (cudaSetDevice(s->p.device) != cudaSuccess) {
+        cudaGetLastError();
+        return LB_ERR_CUDA;
+    }
+    const int N = (int)s->N;
+    const long long T = steps;
+    long long C = checkpoint_every > 0 ? checkpoint_every : (long long)std::ceil(std::sqrt((double)T));
+    if (C < 1) C = 1;
+    const long long K = T > 0 ? (T + C - 1) / C : 0;     // checkpoints at t = 0, C, 2C, ...
+    const size_t slot = (size_t)10 * N;                   // g* (9N) then dpsi (N), floats
+    cudaStream_t st = s->stream;
+
+    // ---- working memory of one call (freed on return)
+    float *ck = nullptr, *seg = nullptr, *lam = nullptr, *scr = nullptr;
+    double *tgt = nullptr, *acc = nullptr, *part = nullptr, *grad_dev = nullptr;
+    unsigned int* cnt = nullptr;
+    auto release = [&]() {
+        void* ptrs[] = {ck, seg, lam, scr, tgt, acc, part, grad_dev, cnt};
+        for (void* q : ptrs)
+            if (q) cudaFree(q);
+        cudaGetLastError();
+    };
+    const bool grad_on_dev = dev_ptr(grad_rho);
+    bool ok = cudaMalloc((void**)&ck, sizeof(float) * slot * (size_t)(K > 0 ? K : 1)) == cudaSuccess &&
+              cudaMalloc((void**)&seg, sizeof(float) * slot * (size_t)C) == cudaSuccess &&
+              cudaMalloc((void**)&lam, sizeof(float) * 18 * (size_t)N) == cudaSuccess &&
+              cudaMalloc((void**)&scr, sizeof(float) * 6 * (size_t)N) == cudaSuccess &&
+              cudaMalloc((void**)&tgt, sizeof(double) * N) == cudaSuccess &&
+              cudaMalloc((void**)&acc, sizeof(double) * 8) == cudaSuccess &&
+              cudaMalloc((void**)&part, sizeof(double) * 4 * 152 * 8) == cudaSuccess &&
+              cudaMalloc((void**)&cnt, sizeof(unsigned int)) == cudaSuccess &&
+              (grad_on_dev || cudaMalloc((void**)&grad_dev, sizeof(double) * N) == cudaSuccess);
+    if (!ok) {
+        release();
+        return LB_ERR_OOM;
+    }
+    auto fail = [&]() {
+        release();
+        s->poisoned = true;
+        return LB_ERR_CUDA;
+    };
+    if (cudaMemcpyAsync(tgt, rho_target, sizeof(double) * N, cudaMemcpyDefault, st) != cudaSuccess ||
+        cudaMemsetAsync(acc, 0, sizeof(double) * 8, st) != cudaSuccess ||
+        cudaMemsetAsync(cnt, 0, sizeof(unsigned int), st) != cudaSuccess)
+        return fail();
+
+    auto save = [&](float* dst, int cur) -> bool {
+        return cudaMemcpyAsync(dst, s->g[cur], sizeof(float) * 9 * N, cudaMemcpyDeviceToDevice,
+                               st) == cudaSuccess &&
+               cudaMemcpyAsync(dst + 9 * (size_t)N, s->dpsi[cur], sizeof(float) * N,
+                               cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    };
+    // ---- forward, checkpointing the state (g*(t-1), dpsi(t)) at t = kC. The
+    // register-prefetch kernel is used here and in the recomputation below, so
+    // the recomputed states are bit-identical to the checkpointed trajectory.
+    Fp32Launch L = s->launch;
+    L.pipeline = 0;
+    for (long long t = 0; t < T; ++t) {
+        if (t % C == 0 && !save(ck + slot * (t / C), s->cur)) return fail();
+        const bool reduce = s->p.trace_every > 0 && (s->t % s->p.trace_every) == 0;
+        if (fp32_step(state_args<float>(s, s->cur), L, reduce, st) != cudaSuccess) return fail();
+        s->cur ^= 1;
+        s->t += 1;
+    }
+
+    AdjArgs A{};
+    A.a = state_args<float>(s, s->cur);
+    A.aw = with_weights(A.a, false);
+    A.ap = with_weights(A.a, true);
+    A.G1 = (float)s->p.G1;
+    A.G2 = (float)s->p.G2;
+    A.sqrt_rho0 = (float)std::sqrt(s->p.rho0);
+    A.rho_target = tgt;
+    A.partials = part;
+    A.counter = cnt;
+    A.Qx = scr;
+    A.Qy = scr + (size_t)N;
+    A.jbx = scr + 2 * (size_t)N;
+    A.jby = scr + 3 * (size_t)N;
+    A.rbar = scr + 4 * (size_t)N;
+    A.dpsidrho = scr + 5 * (size_t)N;
+    float* lamA = lam;
+    float* lamB = lam + 9 * (size_t)N;
+    const int grid = adj_grid(N);
+
+    // ---- terminal: J and l(T)
+    A.g = static_cast<const float*>(s->g[s->cur]);
+    A.dpsi = s->dpsi[s->cur];
+    A.lam = lamA;
+    A.acc = acc;             // acc[0..3] = E, misfit, dE/dG1, dE/dG2
+    k_adj_terminal<<<grid, kAdjThreads, 0, st>>>(A);
+    if (cudaGetLastError() != cudaSuccess) return fail();
+
+    // ---- reverse over the segments, recomputing each from its checkpoint
+    A.acc = acc + 4;         // acc[4], acc[5] = the steps' dJ/dG1, dJ/dG2
+    const StepArgs<float> base = state_args<float>(s, 0);
+    for (long long k = K - 1; k >= 0; --k) {
+        const long long t0 = k * C;
+        const long long n = (k + 1) * C <= T ? C : T - t0;
+        if (cudaMemcpyAsync(seg, ck + slot * k, sizeof(float) * slot, cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess)
+            return fail();
+        for (long long j = 0; j + 1 < n; ++j) {
+            StepArgs<float> a = base;
+            float* in = seg + slot * j;
+            float* out = seg + slot * (j + 1);
+            a.g_in = in;
+            a.g_out = out;
+            a.dpsi_in = in + 9 * (size_t)N;
+            a.dpsi_out = out + 9 * (size_t)N;
+            if (fp32_step(a, L, false, st) != cudaSuccess) return fail();
+        }
+        for (long long j = n - 1; j >= 0; --j) {
+            const float* state = seg + slot * j;
+            A.g = state;
+            A.dpsi = state + 9 * (size_t)N;
+            A.lam_next = lamA;
+            A.lam = lamB;
+            k_adj_pass_a<<<grid, kAdjThreads, 0, st>>>(A);
+            k_adj_pass_b<<<grid, kAdjThreads, 0, st>>>(A);
+            if (cudaGetLastError() != cudaSuccess) return fail();
+            float* tmp = lamA;
+            lamA = lamB;
+            lamB = tmp;
+        }
+    }
+    double* gout = grad_on_dev ? grad_rho : grad_dev;
+    k_adj_grad_init<<<adj_grid(N), kAdjThreads, 0, st>>>(lamA, N, A.a.w0, A.a.w1, A.a.w2, gout);
+    if (cudaGetLastError() != cudaSuccess) return fail();
+    double h[8];
+    if (cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail();
+    if (!grad_on_dev &&
+        cudaMemcpyAsync(grad_rho, grad_dev, sizeof(double) * N, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+        return fail();
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail();
+    release();
+    *J_out = h[0] + h[1];
+    grad_G[0] = h[2] + h[4];
+    grad_G[1] = h[3] + h[5];
+    if (!std::isfinite(*J_out) || !std::isfinite(grad_G[0]) || !std::isfinite(grad_G[1]))
+        return LB_ERR_NONFINITE;
+    return LB_OK;
+}

@@ -1,0 +1,99 @@
+"""GPU adjoint: lb_adjoint (FP32 state and adjoint, FP64 gradient accumulation)
+against the FP64 oracle's reverse sweep, which is itself pinned to central
+finite differences (tests/test_oracle_adjoint.py).
+
+J = E_s(T) + E_m(T) + sum (rho(T) - rho*)^2 on a separate periodic 64 x 64
+lattice (the "64x64 crop" of the 512^2 adjoint workload), G1 = -5, G2 = 0.5,
+rho_init and rho* seeded as the +-1% noise about 0.7 (seeds 11 and 12).
+Bars: J to 1e-6, the G1/G2 gradients to 1e-4 and the field gradient to 1e-4 in
+relative 2-norm — the FP32 forward trajectory and the FP32 adjoint stay within
+about 1e-5 of FP64 over these horizons, well inside the bars."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1008_2865_gb300 import LBError, Lattice, capi, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(n=64):
+    r0 = inputs.noisy_density(n, n, 11, mean=0.7, amp=0.01, mode="rel")
+    tgt = inputs.noisy_density(n, n, 12, mean=0.7, amp=0.01, mode="rel")
+    return r0, tgt
+
+
+@pytest.mark.parametrize("G2,omega,steps", [(0.5, 1.0, 60), (0.0, 1.0, 100), (0.3, 1.3, 40)])
+def test_adjoint_matches_oracle(G2, omega, steps):
+    r0, tgt = _case()
+    Jo, go, gGo = oracle.gradient(r0, tgt, steps, omega=omega, G1=-5.0, G2=G2)
+    with Lattice(r0, omega=omega, G1=-5.0, G2=G2, trace_every=0) as lat:
+        J, g, gG = lat.adjoint(steps, tgt)
+        assert lat.t == steps
+    assert abs(J - Jo) <= 1e-6 * abs(Jo)
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+    for k in range(2):
+        assert abs(gG[k] - gGo[k]) <= 1e-4 * abs(gGo[k])
+
+
+def test_adjoint_is_independent_of_checkpoint_spacing():
+    r0, tgt = _case(48)
+    res = []
+    for C in (0, 1, 7, 30):
+        with Lattice(r0, G1=-5.0, G2=0.5, trace_every=0) as lat:
+            res.append(lat.adjoint(30, tgt, checkpoint_every=C))
+    for J, g, gG in res[1:]:
+        assert J == res[0][0] and gG == res[0][2] and np.array_equal(g, res[0][1])
+
+
+def test_adjoint_forward_equals_plain_run_and_device_output():
+    torch = pytest.importorskip("torch")
+    r0, tgt = _case(96)
+    with Lattice(r0, G1=-5.0, G2=0.5, trace_every=10) as lat:
+        grad = torch.empty((96, 96), dtype=torch.float64, device="cuda")
+        J, _, gG = lat.adjoint(50, torch.from_numpy(tgt).cuda(), grad_rho=grad)
+        rho_a, _, _ = lat.fields()
+        tr_a = lat.trace()
+    with Lattice(r0, G1=-5.0, G2=0.5, trace_every=10) as lat:
+        lat.step(50)
+        rho_b, _, _ = lat.fields()
+        tr_b = lat.trace()
+        J2, g2, gG2 = (None, None, None)
+    assert np.array_equal(rho_a, rho_b) and np.array_equal(tr_a, tr_b)
+    with Lattice(r0, G1=-5.0, G2=0.5, trace_every=0) as lat:
+        J2, g2, gG2 = lat.adjoint(50, tgt)
+    assert J == J2 and gG == gG2 and np.array_equal(grad.cpu().numpy(), g2)
+
+
+def test_autograd_function():
+    torch = pytest.importorskip("torch")
+    from paper_1008_2865_gb300.autograd import LBObjective
+    r0, tgt = _case(40)
+    rho = torch.from_numpy(r0).cuda().requires_grad_(True)
+    G1 = torch.tensor(-5.0, dtype=torch.float64, requires_grad=True)
+    G2 = torch.tensor(0.5, dtype=torch.float64, requires_grad=True)
+    J = LBObjective.apply(rho, G1, G2, torch.from_numpy(tgt).cuda(), 25)
+    (2.0 * J).backward()
+    with Lattice(r0, G1=-5.0, G2=0.5, trace_every=0) as lat:
+        Jr, gr, gGr = lat.adjoint(25, tgt)
+    assert float(J) == Jr
+    assert np.array_equal(rho.grad.cpu().numpy(), 2.0 * gr)
+    assert float(G1.grad) == 2.0 * gGr[0] and float(G2.grad) == 2.0 * gGr[1]
+    # without gradients the forward gives the same J (library energy + misfit)
+    with torch.no_grad():
+        J0 = LBObjective.apply(rho.detach(), G1.detach(), G2.detach(),
+                               torch.from_numpy(tgt).cuda(), 25)
+    assert abs(float(J0) - Jr) <= 1e-6 * abs(Jr)
+
+
+def test_adjoint_arguments():
+    r0, tgt = _case(16)
+    with Lattice(r0, prec="fp64") as lat:
+        with pytest.raises(LBError) as ei:
+            lat.adjoint(5, tgt)
+        assert ei.value.status == capi.LB_ERR_STATE
+    with Lattice(r0) as lat:
+        lat.step(1)
+        with pytest.raises(LBError) as ei:
+            lat.adjoint(5, tgt)
+        assert ei.value.status == capi.LB_ERR_STATE
