@@ -42,10 +42,8 @@ WORKLOAD = ("{n}x{n} periodic D2Q9 two-belt Shan-Chen, FP32 (deviation storage),
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1008_2865_gb300 import replicas
+    return replicas.world()
 
 
 def _peaks():
@@ -283,31 +281,26 @@ def run_ours(args):
 
     from paper_1008_2865_gb300 import Lattice, capi, inputs
 
+    from paper_1008_2865_gb300 import replicas
+
     ws, rank, local = _dist()
     if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        replicas.init("nccl")
     torch.cuda.set_device(local)
     dev = torch.cuda.current_device()
     capi.load(build_if_missing=True)
     stream = torch.cuda.current_stream()
 
     NX = NY = args.size
-    rho0 = inputs.noisy_density(NX, NY, SEED + rank, mean=0.7, amp=0.01, mode="rel")
+    rho0 = inputs.noisy_density(NX, NY, replicas.seed_for_rank(SEED, rank), mean=0.7, amp=0.01,
+                                mode="rel")
 
     def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if ws == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(v, device="cuda")
 
     # ---- device-resident timing: inputs already in HBM
     lat = Lattice(rho0, omega=OMEGA, G1=G1, G2=G2, prec=args.prec, trace_every=TRACE_EVERY,
@@ -414,7 +407,7 @@ def run_ours(args):
         }
     if ws > 1:
         import torch.distributed as dist
-        dist.barrier()
+        replicas.barrier()
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out))
