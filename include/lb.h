@@ -24,7 +24,10 @@
  *   - Work is enqueued on the stream given at init (a cudaStream_t, or NULL
  *     for the legacy default stream) on the device named in lb_params.device.
  *     lb_step is asynchronous; lb_energy, lb_fields and lb_trace synchronise
- *     that stream before they return.
+ *     that stream before they return and report what the kernels flagged
+ *     since: LB_ERR_NONFINITE when a fused energy/mass reduction was not
+ *     finite, LB_ERR_TIMEOUT when a bounded wait ran out.
+ *   - Each call opens an NVTX range named after it (Nsight timelines).
  */
 #ifndef LBSC_LB_H
 #define LBSC_LB_H
@@ -38,7 +41,7 @@ typedef enum {
     LB_ERR_ARG = -1,        /* invalid argument; nothing was changed */
     LB_ERR_CUDA = -2,       /* a CUDA call failed; the state is poisoned */
     LB_ERR_OOM = -3,        /* device allocation failed; nothing was created */
-    LB_ERR_NONFINITE = -4,  /* the lattice holds a NaN/Inf density or energy */
+    LB_ERR_NONFINITE = -4,  /* a NaN/Inf density or energy (a fused reduction or the result) */
     LB_ERR_STATE = -5,      /* call not valid in the state's current condition */
     LB_ERR_TIMEOUT = -6     /* a bounded in-kernel wait ran out; the state is poisoned */
 } lb_status;
@@ -144,6 +147,20 @@ lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta, int pipeline
  * its copies deliver, so the waits run out on purpose; use 0 otherwise.
  * Errors: LB_ERR_ARG (NULL, cycles <= 0). */
 lb_status lb_set_wait_limit(lb_state* s, long long cycles, unsigned int extra_expect_bytes);
+
+/* Checkpoint and resume. A saved state is a small header (lattice size,
+ * precision, time step, reference density) followed by the populations and
+ * psi of the current time step; loading it into a state of the same size and
+ * precision (and, for FP32/FP16, the same rho_ref) continues the run bit for
+ * bit as if it had not been interrupted. The trace ring is not part of it.
+ *   lb_state_bytes   size of the saved form (0 for NULL)
+ *   lb_save_state    write it to dst (host or device memory, >= that size)
+ *   lb_load_state    read it from src into s (host or device memory)
+ * Both synchronise the stream. Errors: LB_ERR_ARG (NULL, short buffer, a
+ * header that does not match s), LB_ERR_STATE, LB_ERR_CUDA. */
+size_t lb_state_bytes(const lb_state* s);
+lb_status lb_save_state(lb_state* s, void* dst, size_t bytes);
+lb_status lb_load_state(lb_state* s, const void* src, size_t bytes);
 
 /* Gradient of J = E_s(T) + E_m(T) + sum_x (rho(x, T) - rho_target(x))^2 — the
  * Sec. 5 pseudo-energy of the state after `steps` steps plus the squared misfit

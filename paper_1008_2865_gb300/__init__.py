@@ -13,7 +13,7 @@ from . import capi, inputs  # noqa: F401
 from .capi import (lb_batch_count, lb_batch_destroy, lb_batch_energy, lb_batch_fields,  # noqa: F401
                    lb_batch_get_launch, lb_batch_init, lb_batch_set_launch, lb_batch_step,
                    lb_batch_time, lb_batch_trace)
-from .capi import lb_adjoint  # noqa: F401
+from .capi import lb_adjoint, lb_load_state, lb_save_state, lb_state_bytes  # noqa: F401
 from .capi import (LBError, lb_destroy, lb_energy, lb_fields, lb_get_launch,  # noqa: F401
                    lb_init, lb_set_launch, lb_set_wait_limit, lb_status_str, lb_step, lb_time,
                    lb_trace, make_params)
@@ -59,6 +59,14 @@ class Lattice:
             return rho, ux, uy
         lb_fields(self.handle, rho, ux, uy)
         return rho, ux, uy
+
+    def save(self, dst=None):
+        """The state in its saved form (NumPy uint8 buffer unless dst is given)."""
+        return lb_save_state(self.handle, dst)
+
+    def load(self, src) -> None:
+        """Resume from a saved form (same size, precision and reference density)."""
+        lb_load_state(self.handle, src)
 
     def adjoint(self, steps: int, rho_target, checkpoint_every: int = 0, grad_rho=None):
         """(J, dJ/drho_init, (dJ/dG1, dJ/dG2)) of J = E_s(T) + E_m(T) + sum (rho(T) - rho*)^2

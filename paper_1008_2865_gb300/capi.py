@@ -105,6 +105,12 @@ def load(build_if_missing: bool = False):
             lib.lb_batch_time.restype = ctypes.c_long
             lib.lb_batch_destroy.argtypes = [vp]
             lib.lb_batch_destroy.restype = None
+            lib.lb_state_bytes.argtypes = [vp]
+            lib.lb_state_bytes.restype = ctypes.c_size_t
+            lib.lb_save_state.argtypes = [vp, vp, ctypes.c_size_t]
+            lib.lb_save_state.restype = ctypes.c_int
+            lib.lb_load_state.argtypes = [vp, vp, ctypes.c_size_t]
+            lib.lb_load_state.restype = ctypes.c_int
             lib.lb_adjoint.argtypes = [vp, ctypes.c_long, vp, ctypes.c_int, dp, vp, dp]
             lib.lb_adjoint.restype = ctypes.c_int
             lib.lb_energy_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
@@ -217,6 +223,24 @@ def lb_energy_noalloc(psi, rho, nx: int, ny: int, G1: float, G2: float, out=None
                                   _ptr(out), ctypes.c_void_p(stream or None))
     _check(st, "lb_energy_noalloc")
     return tuple(float(v) for v in out) if host else out
+
+
+def lb_state_bytes(h: int) -> int:
+    return int(load().lb_state_bytes(ctypes.c_void_p(h)))
+
+
+def lb_save_state(h: int, dst=None):
+    """Save the state into dst (a uint8 array/tensor of lb_state_bytes) or a new NumPy buffer."""
+    n = lb_state_bytes(h)
+    if dst is None:
+        dst = np.empty(n, dtype=np.uint8)
+    _check(load().lb_save_state(ctypes.c_void_p(h), _ptr(dst), n), "lb_save_state")
+    return dst
+
+
+def lb_load_state(h: int, src) -> None:
+    nbytes = src.nbytes if hasattr(src, "nbytes") else src.numel() * src.element_size()
+    _check(load().lb_load_state(ctypes.c_void_p(h), _ptr(src), int(nbytes)), "lb_load_state")
 
 
 def lb_adjoint(h: int, steps: int, rho_target, checkpoint_every: int = 0, grad_rho=None):

@@ -27,6 +27,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lb_device.cuh"
 
 using namespace lbsc;
@@ -275,6 +277,8 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
                                 int checkpoint_every, double* J_out, double* grad_rho,
                                 double* grad_G)
 {
+    nvtxRangePushA("lb_adjoint");
+    struct PopRange { ~PopRange() { nvtxRangePop(); } } pop_range;
     if (!s || steps < 0 || !rho_target || !J_out || !grad_rho || !grad_G || checkpoint_every < 0)
         return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;

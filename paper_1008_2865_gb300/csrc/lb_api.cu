@@ -6,9 +6,19 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lb_internal.h"
 
 using namespace lbsc;
+
+namespace {
+// NVTX range for the duration of an ABI call (visible in Nsight timelines).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace lbsc {
 
@@ -155,7 +165,9 @@ lb_status fail_cuda(lb_state* s)
     return LB_ERR_CUDA;
 }
 
-// Read the kernels' wait-timeout flag (synchronises the stream).
+// Read the kernels' error flags (synchronises the stream): bit 1, a bounded
+// wait ran out (the state is poisoned); bit 2, a fused reduction produced a
+// non-finite mass or energy (the lattice has blown up).
 lb_status check_err(lb_state* s)
 {
     int e = 0;
@@ -163,10 +175,11 @@ lb_status check_err(lb_state* s)
             cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return fail_cuda(s);
-    if (e) {
+    if (e & 1) {
         s->poisoned = true;
         return LB_ERR_TIMEOUT;
     }
+    if (e & 2) return LB_ERR_NONFINITE;
     return LB_OK;
 }
 
@@ -259,6 +272,7 @@ const char* lb_status_str(lb_status st)
 
 lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, void* stream)
 {
+    NvtxRange nvtx_range("lb_init");
     if (!out) return LB_ERR_ARG;
     *out = nullptr;
     if (validate(p) != LB_OK || !rho_init) return LB_ERR_ARG;
@@ -362,6 +376,7 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
 
 lb_status lb_step(lb_state* s, long n)
 {
+    NvtxRange nvtx_range("lb_step");
     if (!s || n < 0) return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;
     if (n == 0) return LB_OK;
@@ -371,6 +386,7 @@ lb_status lb_step(lb_state* s, long n)
 
 lb_status lb_energy(lb_state* s, double out[4])
 {
+    NvtxRange nvtx_range("lb_energy");
     if (!s || !out) return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;
     LB_CUDA(s, cudaSetDevice(s->p.device));
@@ -403,6 +419,7 @@ lb_status lb_energy(lb_state* s, double out[4])
 
 lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy)
 {
+    NvtxRange nvtx_range("lb_fields");
     if (!s) return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;
     LB_CUDA(s, cudaSetDevice(s->p.device));
@@ -470,6 +487,85 @@ lb_status lb_trace(lb_state* s, double* buf, int cap, int* count)
     LB_CUDA(s, cudaStreamSynchronize(s->stream));
     *count = n;
     return check_err(s);
+}
+
+namespace {
+struct SavedHeader {
+    char magic[8];            // "LBSCSTAT"
+    int version, nx, ny, prec;
+    long long t;
+    double rho_ref;
+    long long payload;        // bytes after the header
+};
+constexpr int kSaveVersion = 1;
+
+size_t payload_bytes(const lb_state* s)
+{
+    if (s->p.prec == LB_FP64) return sizeof(double) * 9 * (size_t)s->N;
+    return elem_size(s->p.prec) * 9 * (size_t)s->N + sizeof(float) * (size_t)s->N;
+}
+}  // namespace
+
+size_t lb_state_bytes(const lb_state* s)
+{
+    return s ? sizeof(SavedHeader) + payload_bytes(s) : 0;
+}
+
+lb_status lb_save_state(lb_state* s, void* dst, size_t bytes)
+{
+    if (!s || !dst || bytes < lb_state_bytes(s)) return LB_ERR_ARG;
+    if (s->poisoned) return LB_ERR_STATE;
+    LB_CUDA(s, cudaSetDevice(s->p.device));
+    SavedHeader h{};
+    std::memcpy(h.magic, "LBSCSTAT", 8);
+    h.version = kSaveVersion;
+    h.nx = s->p.nx;
+    h.ny = s->p.ny;
+    h.prec = (int)s->p.prec;
+    h.t = s->t;
+    h.rho_ref = s->rho_ref;
+    h.payload = (long long)payload_bytes(s);
+    char* d = static_cast<char*>(dst);
+    const cudaMemcpyKind k = cudaMemcpyDefault;
+    LB_CUDA(s, cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyDefault, s->stream));
+    d += sizeof(h);
+    if (s->p.prec == LB_FP64) {
+        LB_CUDA(s, cudaMemcpyAsync(d, s->f64[s->cur], sizeof(double) * 9 * s->N, k, s->stream));
+    } else {
+        const size_t gb = elem_size(s->p.prec) * 9 * (size_t)s->N;
+        LB_CUDA(s, cudaMemcpyAsync(d, s->g[s->cur], gb, k, s->stream));
+        LB_CUDA(s, cudaMemcpyAsync(d + gb, s->dpsi[s->cur], sizeof(float) * s->N, k, s->stream));
+    }
+    LB_CUDA(s, cudaStreamSynchronize(s->stream));
+    return LB_OK;
+}
+
+lb_status lb_load_state(lb_state* s, const void* src, size_t bytes)
+{
+    if (!s || !src || bytes < sizeof(SavedHeader)) return LB_ERR_ARG;
+    if (s->poisoned) return LB_ERR_STATE;
+    LB_CUDA(s, cudaSetDevice(s->p.device));
+    SavedHeader h{};
+    LB_CUDA(s, cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDefault, s->stream));
+    LB_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (std::memcmp(h.magic, "LBSCSTAT", 8) != 0 || h.version != kSaveVersion ||
+        h.nx != s->p.nx || h.ny != s->p.ny || h.prec != (int)s->p.prec ||
+        h.payload != (long long)payload_bytes(s) || bytes < lb_state_bytes(s) || h.t < 0)
+        return LB_ERR_ARG;
+    if (s->p.prec != LB_FP64 && h.rho_ref != s->rho_ref) return LB_ERR_ARG;
+    const char* d = static_cast<const char*>(src) + sizeof(h);
+    const cudaMemcpyKind k = cudaMemcpyDefault;
+    if (s->p.prec == LB_FP64) {
+        LB_CUDA(s, cudaMemcpyAsync(s->f64[0], d, sizeof(double) * 9 * s->N, k, s->stream));
+    } else {
+        const size_t gb = elem_size(s->p.prec) * 9 * (size_t)s->N;
+        LB_CUDA(s, cudaMemcpyAsync(s->g[0], d, gb, k, s->stream));
+        LB_CUDA(s, cudaMemcpyAsync(s->dpsi[0], d + gb, sizeof(float) * s->N, k, s->stream));
+    }
+    LB_CUDA(s, cudaStreamSynchronize(s->stream));
+    s->cur = 0;
+    s->t = h.t;
+    return LB_OK;
 }
 
 lb_status lb_get_launch(const lb_state* s, int* block_x, int* rows_per_cta, int* pipeline)

@@ -8,6 +8,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lb_internal.h"
 
 using namespace lbsc;
@@ -87,6 +89,7 @@ lb_status build_tables(lb_batch* b)
         ri.rho_ref = s->rho_ref;
         ri.trace = s->trace;
         ri.trace_count = s->trace_count;
+        ri.err = s->err;
         info.push_back(ri);
         for (int by = 0; by < nty; ++by)
             for (int bx = 0; bx < ntx; ++bx) tiles.push_back(make_int4((int)r, bx, by, 0));
@@ -217,6 +220,8 @@ lb_status lb_batch_init(lb_batch** out, int count, const lb_params* params,
 
 lb_status lb_batch_step(lb_batch* b, long n)
 {
+    nvtxRangePushA("lb_batch_step");
+    struct PopRange { ~PopRange() { nvtxRangePop(); } } pop_range;
     if (!b || n < 0) return LB_ERR_ARG;
     if (b->poisoned) return LB_ERR_STATE;
     if (cudaSetDevice(b->device) != cudaSuccess) return poison(b);

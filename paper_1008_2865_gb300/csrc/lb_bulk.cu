@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
         if (last_block_total<BX>(v, a.partials, a.counter, nb)) {
             const double mass = (double)a.N * (double)a.rho_ref + v[3];
             write_trace_row(a.trace, a.trace_count, a.t, mass, v[0], v[1], v[2]);
+            if (!isfinite(mass) || !isfinite(v[0]) || !isfinite(v[1])) atomicOr(a.err, 2);
         }
     }
 }

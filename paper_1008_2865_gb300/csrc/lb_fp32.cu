@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / B
         if (last_block_total<BX>(v, a.partials, a.counter, nb)) {
             const double mass = (double)a.N * (double)a.rho_ref + v[3];
             write_trace_row(a.trace, a.trace_count, a.t, mass, v[0], v[1], v[2]);
+            if (!isfinite(mass) || !isfinite(v[0]) || !isfinite(v[1])) atomicOr(a.err, 2);
         }
     }
 }
@@ -274,6 +275,7 @@ __global__ void __launch_bounds__(BX)
         const double mass = (double)r.N * r.rho_ref + w[3];
         const long long t = (long long)(*r.trace_count) * trace_every;
         write_trace_row(r.trace, r.trace_count, t, mass, w[0], w[1], w[2]);
+        if (!isfinite(mass) || !isfinite(w[0]) || !isfinite(w[1])) atomicOr(r.err, 2);
     }
 }
 

@@ -45,7 +45,7 @@ struct StepArgs {
     int* trace_count;                // rows ever written
     long long t;                     // time level of the reduced state
     // bounded waits of the bulk-copy kernel
-    int* err;                        // set to nonzero when a wait runs out
+    int* err;                        // error flags: 1 a wait ran out, 2 a reduction was not finite
     long long wait_cycles;           // clock limit of one wait
     unsigned int extra_tx;           // test hook: bytes a unit's barrier expects beyond its copies
 };
@@ -68,6 +68,7 @@ struct BatchRep {
     double rho_ref;
     double* trace;
     int* trace_count;
+    int* err;                  // the replica's error flags
 };
 template <typename T>
 struct BatchLaunch {

@@ -330,3 +330,47 @@ def test_fp32_droplet_count_reproducible():
         rho, _, _, _, _ = _run_gpu(rho0, 1500, G1=-5.0, G2=0.6, trace_every=0)
         counts.append((diag.droplets(rho)[0], diag.perimeter(rho)))
     assert counts[0] == counts[1]
+
+
+# ----------------------------------------------------------------- checkpoint / resume, blow-up
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp16_delta"])
+def test_save_and_resume_is_bit_exact(prec):
+    torch = pytest.importorskip("torch")
+    rho0 = inputs.noisy_density(72, 40, seed=13, mean=0.7, amp=0.01, mode="rel")
+    with Lattice(rho0, prec=prec, G2=0.6, trace_every=7) as a:
+        a.step(30)
+        saved = a.save()
+        a.step(40)
+        ref = a.fields()
+        tr_ref = a.trace()
+    # into a fresh state of the same shape (other initial density, same rho_ref)
+    with Lattice(rho0[::-1].copy(), prec=prec, G2=0.6, trace_every=7,
+                 rho_ref=float(np.float32(rho0.mean()))) as b:
+        b.load(saved)
+        assert b.t == 30
+        b.step(40)
+        got = b.fields()
+        tr = b.trace()
+    for u, v in zip(got, ref):
+        assert np.array_equal(u, v)
+    # the rows after the resume point agree bit for bit
+    assert np.array_equal(tr[tr[:, 0] >= 30], tr_ref[tr_ref[:, 0] >= 30])
+    # device buffers work too, and a mismatching header is refused
+    with Lattice(rho0, prec=prec, G2=0.6, trace_every=0) as c:
+        dev = torch.empty(capi.lb_state_bytes(c.handle), dtype=torch.uint8, device="cuda")
+        c.save(dev)
+        c.load(dev)
+    with Lattice(inputs.noisy_density(40, 72, seed=1), prec=prec) as d:
+        with pytest.raises(LBError):
+            d.load(saved)
+
+
+def test_blow_up_is_reported_as_nonfinite():
+    """An absurd coupling drives the lattice to NaN; the fused reduction flags it and the
+    next synchronising call reports LB_ERR_NONFINITE instead of returning garbage silently."""
+    rho0 = inputs.noisy_density(32, 32, seed=2, mean=0.7, amp=0.05)
+    with Lattice(rho0, G1=-400.0, G2=0.0, trace_every=1) as lat:
+        lat.step(300)
+        with pytest.raises(LBError) as ei:
+            lat.trace()
+        assert ei.value.status == capi.LB_ERR_NONFINITE
