@@ -148,6 +148,17 @@ lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta, int pipeline
  * Errors: LB_ERR_ARG (NULL, cycles <= 0). */
 lb_status lb_set_wait_limit(lb_state* s, long long cycles, unsigned int extra_expect_bytes);
 
+/* Guard check (debugging without a memory checker). Every device buffer of a
+ * state is allocated with a 256-byte guard region on each side holding the
+ * byte 0xA5; *damaged receives the number of buffers whose guards no longer
+ * hold it, i.e. that some kernel wrote outside. Synchronises the stream.
+ * Errors: LB_ERR_ARG, LB_ERR_CUDA. */
+lb_status lb_check_guards(lb_state* s, int* damaged);
+/* Test hook for the guard check: overwrite one byte of the tail guard of the
+ * state's buffer number `buffer` (0-based, in allocation order) with a host-side
+ * cudaMemset. Errors: LB_ERR_ARG (NULL or no such buffer), LB_ERR_CUDA. */
+lb_status lb_debug_damage_guard(lb_state* s, int buffer);
+
 /* Checkpoint and resume. A saved state is a small header (lattice size,
  * precision, time step, reference density) followed by the populations and
  * psi of the current time step; loading it into a state of the same size and
@@ -211,6 +222,8 @@ lb_status lb_batch_trace(lb_batch* b, int replica, double* buf, int cap, int* co
  * (use_graph 0 or 1). Defaults: 128, 32, 1. */
 lb_status lb_batch_get_launch(const lb_batch* b, int* block_x, int* rows_per_cta, int* use_graph);
 lb_status lb_batch_set_launch(lb_batch* b, int block_x, int rows_per_cta, int use_graph);
+/* lb_check_guards summed over the replicas. */
+lb_status lb_batch_check_guards(lb_batch* b, int* damaged);
 /* Number of replicas (-1 for NULL) and steps taken (-1 for NULL). */
 int lb_batch_count(const lb_batch* b);
 long lb_batch_time(const lb_batch* b);

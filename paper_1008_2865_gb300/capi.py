@@ -99,12 +99,18 @@ def load(build_if_missing: bool = False):
             lib.lb_batch_get_launch.restype = ctypes.c_int
             lib.lb_batch_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.lb_batch_set_launch.restype = ctypes.c_int
+            lib.lb_batch_check_guards.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+            lib.lb_batch_check_guards.restype = ctypes.c_int
             lib.lb_batch_count.argtypes = [vp]
             lib.lb_batch_count.restype = ctypes.c_int
             lib.lb_batch_time.argtypes = [vp]
             lib.lb_batch_time.restype = ctypes.c_long
             lib.lb_batch_destroy.argtypes = [vp]
             lib.lb_batch_destroy.restype = None
+            lib.lb_check_guards.argtypes = [vp, ip]
+            lib.lb_check_guards.restype = ctypes.c_int
+            lib.lb_debug_damage_guard.argtypes = [vp, ctypes.c_int]
+            lib.lb_debug_damage_guard.restype = ctypes.c_int
             lib.lb_state_bytes.argtypes = [vp]
             lib.lb_state_bytes.restype = ctypes.c_size_t
             lib.lb_save_state.argtypes = [vp, vp, ctypes.c_size_t]
@@ -225,6 +231,17 @@ def lb_energy_noalloc(psi, rho, nx: int, ny: int, G1: float, G2: float, out=None
     return tuple(float(v) for v in out) if host else out
 
 
+def lb_check_guards(h: int) -> int:
+    """Number of the state's device buffers whose guard regions were overwritten."""
+    n = ctypes.c_int(0)
+    _check(load().lb_check_guards(ctypes.c_void_p(h), ctypes.byref(n)), "lb_check_guards")
+    return n.value
+
+
+def lb_debug_damage_guard(h: int, buffer: int) -> None:
+    _check(load().lb_debug_damage_guard(ctypes.c_void_p(h), int(buffer)), "lb_debug_damage_guard")
+
+
 def lb_state_bytes(h: int) -> int:
     return int(load().lb_state_bytes(ctypes.c_void_p(h)))
 
@@ -309,6 +326,13 @@ def lb_batch_get_launch(h: int):
 def lb_batch_set_launch(h: int, block_x: int, rows_per_cta: int, use_graph: int = 1) -> None:
     _check(load().lb_batch_set_launch(ctypes.c_void_p(h), int(block_x), int(rows_per_cta),
                                       int(use_graph)), "lb_batch_set_launch")
+
+
+def lb_batch_check_guards(h: int) -> int:
+    n = ctypes.c_int(0)
+    _check(load().lb_batch_check_guards(ctypes.c_void_p(h), ctypes.byref(n)),
+           "lb_batch_check_guards")
+    return n.value
 
 
 def lb_batch_count(h) -> int:

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -21,6 +22,26 @@ struct NvtxRange {
 }  // namespace
 
 namespace lbsc {
+
+void* state_alloc(lb_state* s, size_t bytes)
+{
+    // round the usable size up so the tail guard starts 256-byte aligned
+    const size_t body = (bytes + kGuardBytes - 1) / kGuardBytes * kGuardBytes;
+    void* base = nullptr;
+    if (cudaMalloc(&base, body + 2 * kGuardBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    char* b = static_cast<char*>(base);
+    if (cudaMemsetAsync(b, kGuardByte, kGuardBytes, s->stream) != cudaSuccess ||
+        cudaMemsetAsync(b + kGuardBytes + body, kGuardByte, kGuardBytes, s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(base);
+        return nullptr;
+    }
+    s->allocs.push_back({base, body});
+    return b + kGuardBytes;
+}
 
 Couplings couplings(double G1, double G2)
 {
@@ -193,11 +214,7 @@ void free_state(lb_state* s)
     if (!s) return;
     cudaSetDevice(s->p.device);
     cudaStreamSynchronize(s->stream);
-    void* ptrs[] = {s->g[0], s->g[1], s->dpsi[0], s->dpsi[1], s->f64[0], s->f64[1], s->psi64,
-                    s->rho64, s->partials, s->counter, s->trace, s->trace_count, s->res,
-                    s->flag, s->field_tmp, s->err};
-    for (void* q : ptrs)
-        if (q) cudaFree(q);
+    for (const lb_state::Alloc& a : s->allocs) cudaFree(a.base);
     cudaGetLastError();
     delete s;
 }
@@ -288,11 +305,8 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
         return LB_ERR_CUDA;
     }
     auto alloc = [&](void** q, size_t bytes) -> bool {
-        if (cudaMalloc(q, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        return true;
+        *q = state_alloc(s, bytes);
+        return *q != nullptr;
     };
     s->launch = default_launch(p->nx, p->ny, p->prec);
     size_t nblk_step = (size_t)fp32_grid_blocks(p->nx, p->ny, Fp32Launch{64, 16, 0});
@@ -322,9 +336,10 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
         return LB_ERR_OOM;
     }
     // rho_init on the device (copied when it is host memory)
-    double* rho_dev = nullptr;
+    double* rho_dev = nullptr;   // a temporary, not one of the state's guarded buffers
     const bool dev_src = is_device_ptr(rho_init);
-    if (!alloc((void**)&rho_dev, sizeof(double) * N)) {
+    if (cudaMalloc((void**)&rho_dev, sizeof(double) * N) != cudaSuccess) {
+        cudaGetLastError();
         free_state(s);
         return LB_ERR_OOM;
     }
@@ -431,7 +446,8 @@ lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy)
         double* dst = outs[k];
         if (!dev) {
             if (!s->field_tmp) {
-                if (cudaMalloc((void**)&s->field_tmp, sizeof(double) * N) != cudaSuccess) {
+                s->field_tmp = static_cast<double*>(state_alloc(s, sizeof(double) * N));
+                if (!s->field_tmp) {
                     cudaGetLastError();
                     s->field_tmp = nullptr;
                     return LB_ERR_OOM;
@@ -505,6 +521,38 @@ size_t payload_bytes(const lb_state* s)
     return elem_size(s->p.prec) * 9 * (size_t)s->N + sizeof(float) * (size_t)s->N;
 }
 }  // namespace
+
+lb_status lb_check_guards(lb_state* s, int* damaged)
+{
+    if (!s || !damaged) return LB_ERR_ARG;
+    *damaged = 0;
+    LB_CUDA(s, cudaSetDevice(s->p.device));
+    LB_CUDA(s, cudaStreamSynchronize(s->stream));
+    std::vector<unsigned char> h(2 * kGuardBytes);
+    for (const lb_state::Alloc& a : s->allocs) {
+        const char* b = static_cast<const char*>(a.base);
+        LB_CUDA(s, cudaMemcpy(h.data(), b, kGuardBytes, cudaMemcpyDeviceToHost));
+        LB_CUDA(s, cudaMemcpy(h.data() + kGuardBytes, b + kGuardBytes + a.bytes, kGuardBytes,
+                              cudaMemcpyDeviceToHost));
+        for (unsigned char c : h)
+            if (c != kGuardByte) {
+                ++*damaged;
+                break;
+            }
+    }
+    return LB_OK;
+}
+
+lb_status lb_debug_damage_guard(lb_state* s, int buffer)
+{
+    if (!s || buffer < 0 || buffer >= (int)s->allocs.size()) return LB_ERR_ARG;
+    LB_CUDA(s, cudaSetDevice(s->p.device));
+    const lb_state::Alloc& a = s->allocs[(size_t)buffer];
+    char* tail = static_cast<char*>(a.base) + kGuardBytes + a.bytes;
+    LB_CUDA(s, cudaMemsetAsync(tail + 17, 0x00, 1, s->stream));
+    LB_CUDA(s, cudaStreamSynchronize(s->stream));
+    return LB_OK;
+}
 
 size_t lb_state_bytes(const lb_state* s)
 {

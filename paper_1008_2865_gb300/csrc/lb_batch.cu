@@ -291,6 +291,19 @@ lb_status lb_batch_set_launch(lb_batch* b, int block_x, int rows_per_cta, int us
     return build_tables(b);
 }
 
+lb_status lb_batch_check_guards(lb_batch* b, int* damaged)
+{
+    if (!b || !damaged) return LB_ERR_ARG;
+    *damaged = 0;
+    for (lb_state* s : b->reps) {
+        int d = 0;
+        const lb_status st = lb_check_guards(s, &d);
+        if (st != LB_OK) return st;
+        *damaged += d;
+    }
+    return LB_OK;
+}
+
 int lb_batch_count(const lb_batch* b) { return b ? (int)b->reps.size() : -1; }
 
 long lb_batch_time(const lb_batch* b) { return b ? (long)b->t : -1; }

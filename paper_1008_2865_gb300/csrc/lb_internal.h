@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cstdint>
+#include <vector>
 
 #include "lb.h"
 
@@ -156,7 +157,21 @@ struct lb_state {
     double* res = nullptr;         // 4 doubles of results
     int* flag = nullptr;
     double* field_tmp = nullptr;   // N doubles, allocated on the first host-destined lb_fields
+    // every device buffer of the state, with a guard region on each side
+    struct Alloc {
+        void* base;
+        size_t bytes;
+    };
+    std::vector<Alloc> allocs;
 };
+
+namespace lbsc {
+constexpr size_t kGuardBytes = 256;              // guard region on each side of a buffer
+constexpr unsigned char kGuardByte = 0xA5;       // the pattern the guards hold
+// Allocate `bytes` for a state with guards on both sides (pattern written on
+// the state's stream); returns the usable pointer or nullptr.
+void* state_alloc(lb_state* s, size_t bytes);
+}  // namespace lbsc
 
 namespace lbsc {
 template <typename T>

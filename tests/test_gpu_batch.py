@@ -29,6 +29,7 @@ def test_batch_matches_single_runs_bit_for_bit(use_graph, launch):
         b.set_launch(launch[0], launch[1], use_graph)
         b.step(steps)
         assert b.t == steps and len(b) == len(rhos)
+        assert capi.lb_batch_check_guards(b.handle) == 0
         got = [(b.fields(i), b.trace(i), b.energy(i)) for i in range(len(rhos))]
     for i, r in enumerate(rhos):
         with Lattice(r, G1=-5.0, G2=G2S[i], trace_every=10) as lat:

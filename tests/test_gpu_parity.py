@@ -42,6 +42,8 @@ def _run_gpu(rho0, steps, prec="fp32", launch=None, **kw):
         tr = lat.trace()
         en = lat.energy()
         assert lat.t == steps
+        # no kernel wrote outside any of the state's buffers
+        assert capi.lb_check_guards(lat.handle) == 0
     return rho, ux, uy, tr, en
 
 
@@ -235,6 +237,20 @@ def test_device_pointers_and_partial_fields():
         only_ux = np.empty((30, 40))
         lat.fields(ux=only_ux)
         assert np.array_equal(only_ux, h_ux)
+
+
+def test_guard_check_sees_a_write_outside_a_buffer():
+    """The guard check is not vacuous: a byte changed just past a buffer (by a host-side
+    cudaMemset through the test hook, never by a kernel) is reported, buffer by buffer."""
+    with Lattice(inputs.noisy_density(40, 30, seed=1)) as lat:
+        lat.step(3)
+        assert capi.lb_check_guards(lat.handle) == 0
+        capi.lb_debug_damage_guard(lat.handle, 0)
+        assert capi.lb_check_guards(lat.handle) == 1
+        capi.lb_debug_damage_guard(lat.handle, 3)
+        assert capi.lb_check_guards(lat.handle) == 2
+        with pytest.raises(LBError):
+            capi.lb_debug_damage_guard(lat.handle, 10_000)
 
 
 def test_pipeline_availability():
