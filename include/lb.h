@@ -158,6 +158,10 @@ lb_status lb_check_guards(lb_state* s, int* damaged);
  * state's buffer number `buffer` (0-based, in allocation order) with a host-side
  * cudaMemset. Errors: LB_ERR_ARG (NULL or no such buffer), LB_ERR_CUDA. */
 lb_status lb_debug_damage_guard(lb_state* s, int buffer);
+/* Test hook for the allocation-failure path: after `after` more state buffer
+ * allocations succeed, the next one fails once (as if the device were out of
+ * memory); a negative value disarms it. Process-wide. */
+void lb_debug_fail_alloc(int after);
 
 /* Checkpoint and resume. A saved state is a small header (lattice size,
  * precision, time step, reference density) followed by the populations and

@@ -109,6 +109,8 @@ def load(build_if_missing: bool = False):
             lib.lb_batch_destroy.restype = None
             lib.lb_check_guards.argtypes = [vp, ip]
             lib.lb_check_guards.restype = ctypes.c_int
+            lib.lb_debug_fail_alloc.argtypes = [ctypes.c_int]
+            lib.lb_debug_fail_alloc.restype = None
             lib.lb_debug_damage_guard.argtypes = [vp, ctypes.c_int]
             lib.lb_debug_damage_guard.restype = ctypes.c_int
             lib.lb_state_bytes.argtypes = [vp]
@@ -236,6 +238,10 @@ def lb_check_guards(h: int) -> int:
     n = ctypes.c_int(0)
     _check(load().lb_check_guards(ctypes.c_void_p(h), ctypes.byref(n)), "lb_check_guards")
     return n.value
+
+
+def lb_debug_fail_alloc(after: int) -> None:
+    load().lb_debug_fail_alloc(int(after))
 
 
 def lb_debug_damage_guard(h: int, buffer: int) -> None:

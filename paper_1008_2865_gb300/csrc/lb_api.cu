@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -23,8 +24,17 @@ struct NvtxRange {
 
 namespace lbsc {
 
+// Test hook: allocations left before one is made to fail (-1: never).
+static std::atomic<int> g_fail_allocs_after{-1};
+
 void* state_alloc(lb_state* s, size_t bytes)
 {
+    {
+        int left = g_fail_allocs_after.load();
+        while (left >= 0 && !g_fail_allocs_after.compare_exchange_weak(left, left - 1)) {
+        }
+        if (left == 0) return nullptr;   // the hook's failure (counter is now -1: disarmed)
+    }
     // round the usable size up so the tail guard starts 256-byte aligned
     const size_t body = (bytes + kGuardBytes - 1) / kGuardBytes * kGuardBytes;
     void* base = nullptr;
@@ -541,6 +551,11 @@ lb_status lb_check_guards(lb_state* s, int* damaged)
             }
     }
     return LB_OK;
+}
+
+void lb_debug_fail_alloc(int after)
+{
+    lbsc::g_fail_allocs_after.store(after < 0 ? -1 : after);
 }
 
 lb_status lb_debug_damage_guard(lb_state* s, int buffer)

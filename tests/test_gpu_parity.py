@@ -7,6 +7,8 @@ Bars (written here, from the targets the method is held to):
               max|d u| / max|u| (u starts at 0, so pointwise relative error is
               ill-posed); mass to 1e-6; pseudo-energy trace to 1e-4.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -390,3 +392,59 @@ def test_blow_up_is_reported_as_nonfinite():
         with pytest.raises(LBError) as ei:
             lat.trace()
         assert ei.value.status == capi.LB_ERR_NONFINITE
+
+
+# ----------------------------------------------------------------- invariants on the GPU
+def test_uniform_state_stays_exactly_uniform_gpu():
+    for prec in ("fp32", "fp64", "fp16_delta"):
+        rho0 = np.full((40, 64), 0.7)
+        rho, ux, uy, tr, en = _run_gpu(rho0, 50, prec=prec, G1=-5.0, G2=0.6, trace_every=10)
+        assert np.max(np.abs(rho - 0.7)) <= (1e-14 if prec == "fp64" else 1e-7)
+        assert np.max(np.abs(ux)) <= 1e-15 and np.max(np.abs(uy)) <= 1e-15
+
+
+def test_uniform_energy_closed_form_gpu():
+    """Sec. 5: uniform psi gives E_s + E_m = E_bulk = A1/2 N psi^2, E_m = G2/2 N psi^2 596/15120."""
+    psi = 1.0 - math.exp(-0.7)
+    N = 40 * 64
+    for prec, tol in (("fp64", 1e-13), ("fp32", 1e-6)):
+        with Lattice(np.full((40, 64), 0.7), prec=prec, G1=-5.0, G2=0.6) as lat:
+            es, em, eb, mass = lat.energy()
+        assert abs(eb - (-4.4) / 2 * N * psi * psi) <= tol * abs(eb)
+        assert abs(es + em - eb) <= tol * abs(eb)
+        assert abs(em - 0.6 / 2 * N * psi * psi * 596 / 15120) <= tol * abs(em) + 1e-12
+        assert abs(mass - 0.7 * N) <= tol * mass
+
+
+def test_total_momentum_stays_zero_gpu():
+    """sum_x F = 0 for the antisymmetric stencil, so sum rho u stays at its initial 0."""
+    rho0 = inputs.noisy_density(96, 64, seed=21, mean=0.7, amp=0.05)
+    for prec, tol in (("fp64", 1e-11), ("fp32", 1e-5)):
+        rho, ux, uy, _, _ = _run_gpu(rho0, 300, prec=prec, G1=-5.0, G2=0.6, trace_every=0)
+        assert rho.max() - rho.min() > 0.1
+        assert abs((rho * ux).sum()) <= tol and abs((rho * uy).sum()) <= tol
+
+
+def test_translation_is_exact_gpu():
+    """Every site runs the same arithmetic whatever tile it falls in: a periodic shift of
+    the input shifts the fields bit for bit (FP32 fused kernel, odd shape)."""
+    rho0 = inputs.noisy_density(301, 77, seed=22, mean=0.7, amp=0.01, mode="rel")
+    a = _run_gpu(rho0, 40, G1=-5.0, G2=0.6, trace_every=0, rho_ref=0.7)
+    b = _run_gpu(np.roll(rho0, (5, -33), (0, 1)), 40, G1=-5.0, G2=0.6, trace_every=0, rho_ref=0.7)
+    for u, v in zip(a[:3], b[:3]):
+        assert np.array_equal(np.roll(u, (5, -33), (0, 1)), v)
+
+
+def test_allocation_failure_returns_oom_and_cleans_up():
+    rho0 = inputs.noisy_density(64, 64, seed=1)
+    for after in (0, 3, 7):
+        capi.lb_debug_fail_alloc(after)
+        try:
+            with pytest.raises(LBError) as ei:
+                Lattice(rho0)
+            assert ei.value.status == capi.LB_ERR_OOM
+        finally:
+            capi.lb_debug_fail_alloc(-1)
+    # the library keeps working afterwards
+    rho, _, _, _, _ = _run_gpu(rho0, 5, G1=-5.0, G2=0.0, trace_every=0)
+    assert np.isfinite(rho).all()
