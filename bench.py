@@ -1,7 +1,7 @@
 """Benchmark: MLUPS of the fused FP32 two-belt Shan–Chen step on GB300.
 
-One "step" is one pass of the whole hot path over the lattice: pull
-streaming, moments, psi, the two-belt force, velocity-shifted BGK collision,
+One "step" is one pass of the whole hot path over the lattice: moments,
+psi, the two-belt force, velocity-shifted BGK collision, streaming (on chip),
 psi of the next state, and (every 10th step) the fused pseudo-energy and mass
 reduction. The workload is the 8192 x 8192 periodic lattice, FP32, G1 = -5,
 G2 = 0.6, rho = 0.7 (1 +- 1%) seeded noise — the bandwidth-roofline case.

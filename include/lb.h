@@ -83,7 +83,8 @@ typedef struct lb_state lb_state;   /* opaque; owns device memory */
  *   out       receives the new state (set to NULL on failure)
  *   p         parameters; validated: nx, ny >= 5, 0 < omega < 2, finite G1
  *             and G2, rho0 > 0, trace_every >= 0, known psi_form and prec,
- *             nx*ny*9 below 2^31
+ *             nx*ny*9 and 288*ceil(nx/32)*ny (the populations of an FP32 or
+ *             FP16 state, stored in 32-column tiles) below 2^31
  *   rho_init  N initial densities, host or device, each finite and > 0
  *   stream    cudaStream_t (as void*) used by every later call on the state
  * Errors: LB_ERR_ARG (bad parameter or rho_init), LB_ERR_OOM, LB_ERR_CUDA. */
@@ -128,7 +129,7 @@ lb_status lb_trace(lb_state* s, double* buf, int cap, int* count);
  *      block_x - 2 output columns per CTA);
  *   1  bulk-copy rings: the bulk-copy (TMA) engine stages whole rows in shared
  *      memory several rows ahead (block_x in {64, 128, 256}; needs nx a
- *      multiple of 16 bytes' worth of elements and nx >= block_x + 8).
+ *      multiple of 32 and nx >= block_x + 64).
  * lb_init starts with pipeline 0 (measured the faster of the two on GB300 for
  * the 8192 x 8192 lattice). rows_per_cta is in
  * [16, 4096]. The shape changes how the work is split, not the trajectory;

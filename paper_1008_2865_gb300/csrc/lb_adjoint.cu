@@ -57,21 +57,11 @@ __device__ __forceinline__ void gather5(const float* __restrict__ fld, int x, in
     }
 }
 
-// Pulled deviations f_i(x, y) - w_i rho_ref from post-collision deviations g*.
-__device__ __forceinline__ void pull_site(const float* __restrict__ g, int N, int x, int y, int nx,
-                                          int ny, float f[9])
+// Deviations f_i(x, y) - w_i rho_ref of state t, read from the tiled populations.
+__device__ __forceinline__ void site_f(const float* __restrict__ g, int pitch, int x, int y,
+                                       float f[9])
 {
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const int om = (y == 0 ? ny - 1 : y - 1) * nx, oc = y * nx, op = (y == ny - 1 ? 0 : y + 1) * nx;
-    f[0] = __ldg(g + oc + x);
-    f[1] = __ldg(g + N + oc + xm);
-    f[2] = __ldg(g + 2 * N + om + x);
-    f[3] = __ldg(g + 3 * N + oc + xp);
-    f[4] = __ldg(g + 4 * N + op + x);
-    f[5] = __ldg(g + 5 * N + om + xm);
-    f[6] = __ldg(g + 6 * N + om + xp);
-    f[7] = __ldg(g + 7 * N + op + xp);
-    f[8] = __ldg(g + 8 * N + op + xm);
+    load_site(f, g + y * pitch + tcol(x));
 }
 
 __constant__ int ACX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -83,7 +73,7 @@ struct AdjArgs {
     StepArgs<float> ap;       // couplings replaced by the E(8) weights (S_p)
     float G1, G2;
     float sqrt_rho0;
-    const float* g;           // g*(t-1): pull gives f(t)
+    const float* g;           // tiled f(t) - w rho_ref
     const float* dpsi;        // dpsi(t)
     const float* lam_next;    // [9][N] dJ/df(t+1)
     float* lam;               // [9][N] dJ/df(t)
@@ -116,7 +106,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A)
     for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
         const int y = s / nx, x = s % nx;
         float f[9];
-        pull_site(A.g, N, x, y, nx, ny, f);
+        site_f(A.g, a.pitch, x, y, f);
         const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
         const float rho = a.rho_ref + d;
         float p[5][5];
@@ -157,7 +147,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
     for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
         const int y = s / nx, x = s % nx;
         float f[9];
-        pull_site(A.g, N, x, y, nx, ny, f);
+        site_f(A.g, a.pitch, x, y, f);
         const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
         const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
         const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
@@ -292,7 +282,8 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
     long long C = checkpoint_every > 0 ? checkpoint_every : (long long)std::ceil(std::sqrt((double)T));
     if (C < 1) C = 1;
     const long long K = T > 0 ? (T + C - 1) / C : 0;     // checkpoints at t = 0, C, 2C, ...
-    const size_t slot = (size_t)10 * N;                   // g* (9N) then dpsi (N), floats
+    const size_t GE = (size_t)g_elems(s->p.nx, s->p.ny);
+    const size_t slot = GE + (size_t)N;                   // populations (GE) then dpsi (N), floats
     cudaStream_t st = s->stream;
 
     // ---- working memory of one call (freed on return)
@@ -330,12 +321,12 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
         return fail();
 
     auto save = [&](float* dst, int cur) -> bool {
-        return cudaMemcpyAsync(dst, s->g[cur], sizeof(float) * 9 * N, cudaMemcpyDeviceToDevice,
+        return cudaMemcpyAsync(dst, s->g[cur], sizeof(float) * GE, cudaMemcpyDeviceToDevice,
                                st) == cudaSuccess &&
-               cudaMemcpyAsync(dst + 9 * (size_t)N, s->dpsi[cur], sizeof(float) * N,
+               cudaMemcpyAsync(dst + GE, s->dpsi[cur], sizeof(float) * N,
                                cudaMemcpyDeviceToDevice, st) == cudaSuccess;
     };
-    // ---- forward, checkpointing the state (g*(t-1), dpsi(t)) at t = kC. The
+    // ---- forward, checkpointing the state (g(t), dpsi(t)) at t = kC. The
     // register-prefetch kernel is used here and in the recomputation below, so
     // the recomputed states are bit-identical to the checkpointed trajectory.
     Fp32Launch L = s->launch;
@@ -391,14 +382,14 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
             float* out = seg + slot * (j + 1);
             a.g_in = in;
             a.g_out = out;
-            a.dpsi_in = in + 9 * (size_t)N;
-            a.dpsi_out = out + 9 * (size_t)N;
+            a.dpsi_in = in + GE;
+            a.dpsi_out = out + GE;
             if (fp32_step(a, L, false, st) != cudaSuccess) return fail();
         }
         for (long long j = n - 1; j >= 0; --j) {
             const float* state = seg + slot * j;
             A.g = state;
-            A.dpsi = state + 9 * (size_t)N;
+            A.dpsi = state + GE;
             A.lam_next = lamA;
             A.lam = lamB;
             k_adj_pass_a<<<grid, kAdjThreads, 0, st>>>(A);

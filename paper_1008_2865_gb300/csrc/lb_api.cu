@@ -92,6 +92,7 @@ lb_status validate(const lb_params* p)
     if (!p) return LB_ERR_ARG;
     if (p->nx < 5 || p->ny < 5) return LB_ERR_ARG;
     if ((long long)p->nx * p->ny * 9 >= (1LL << 31)) return LB_ERR_ARG;
+    if (g_elems(p->nx, p->ny) >= (1LL << 31)) return LB_ERR_ARG;   // 32-bit indices in the steps
     if (!(p->omega > 0.0 && p->omega < 2.0)) return LB_ERR_ARG;
     if (!std::isfinite(p->G1) || !std::isfinite(p->G2)) return LB_ERR_ARG;
     if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) return LB_ERR_ARG;
@@ -106,13 +107,13 @@ lb_status validate(const lb_params* p)
 // Default launch shape: 128-thread strips with the register-prefetch
 // pipeline (measured faster than the bulk-copy rings on GB300 for the 8192^2
 // lattice; the tuner may still pick the rings), rows chosen for about four
-// waves of 8 resident CTAs per SM on a 152-SM part, at least 16 rows.
+// waves of 10 resident CTAs per SM on a 152-SM part, at least 16 rows.
 Fp32Launch default_launch(int nx, int ny, lb_precision prec)
 {
     (void)prec;
     Fp32Launch L{128, 64, 0};
     const long long strips = (nx + 125) / 126;
-    const long long target = 152LL * 8 * 4;
+    const long long target = 152LL * 10 * 4;
     long long rows = (strips * ny + target - 1) / target;
     if (rows < 16) rows = 16;
     if (rows > 512) rows = 512;
@@ -152,6 +153,8 @@ StepArgs<T> state_args(const lb_state* s, int cur)
     a.ny = p.ny;
     a.rows = s->launch.rows;
     a.N = s->N;
+    a.pitch = g_pitch(p.nx);
+    a.npitch = (int)g_elems(p.nx, p.ny);
     a.omega = (float)p.omega;
     a.omc = (float)(1.0 - p.omega);
     a.inv_omega = (float)(1.0 / p.omega);
@@ -337,7 +340,8 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
              alloc((void**)&s->rho64, sizeof(double) * N);
     } else if (ok) {
         const size_t es = elem_size(p->prec);
-        ok = alloc(&s->g[0], 9 * es * N) && alloc(&s->g[1], 9 * es * N) &&
+        const size_t gb = es * (size_t)g_elems(p->nx, p->ny);
+        ok = alloc(&s->g[0], gb) && alloc(&s->g[1], gb) &&
              alloc((void**)&s->dpsi[0], sizeof(float) * N) &&
              alloc((void**)&s->dpsi[1], sizeof(float) * N);
     }
@@ -367,6 +371,13 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
         cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->err, 0, sizeof(int), s->stream) != cudaSuccess)
         return bail(LB_ERR_CUDA);
+    if (p->prec != LB_FP64) {
+        // the padding columns of the tiled populations hold zeros in both buffers
+        const size_t gb = elem_size(p->prec) * (size_t)g_elems(p->nx, p->ny);
+        if (cudaMemsetAsync(s->g[0], 0, gb, s->stream) != cudaSuccess ||
+            cudaMemsetAsync(s->g[1], 0, gb, s->stream) != cudaSuccess)
+            return bail(LB_ERR_CUDA);
+    }
     if (rho_check_sum(rho_dev, N, s->partials, s->counter, s->res, s->flag, s->stream) !=
         cudaSuccess)
         return bail(LB_ERR_CUDA);
@@ -523,12 +534,13 @@ struct SavedHeader {
     double rho_ref;
     long long payload;        // bytes after the header
 };
-constexpr int kSaveVersion = 1;
+constexpr int kSaveVersion = 2;   // 2: tiled populations of state t
 
 size_t payload_bytes(const lb_state* s)
 {
     if (s->p.prec == LB_FP64) return sizeof(double) * 9 * (size_t)s->N;
-    return elem_size(s->p.prec) * 9 * (size_t)s->N + sizeof(float) * (size_t)s->N;
+    return elem_size(s->p.prec) * (size_t)g_elems(s->p.nx, s->p.ny) +
+           sizeof(float) * (size_t)s->N;
 }
 }  // namespace
 
@@ -595,7 +607,7 @@ lb_status lb_save_state(lb_state* s, void* dst, size_t bytes)
     if (s->p.prec == LB_FP64) {
         LB_CUDA(s, cudaMemcpyAsync(d, s->f64[s->cur], sizeof(double) * 9 * s->N, k, s->stream));
     } else {
-        const size_t gb = elem_size(s->p.prec) * 9 * (size_t)s->N;
+        const size_t gb = elem_size(s->p.prec) * (size_t)g_elems(s->p.nx, s->p.ny);
         LB_CUDA(s, cudaMemcpyAsync(d, s->g[s->cur], gb, k, s->stream));
         LB_CUDA(s, cudaMemcpyAsync(d + gb, s->dpsi[s->cur], sizeof(float) * s->N, k, s->stream));
     }
@@ -621,7 +633,7 @@ lb_status lb_load_state(lb_state* s, const void* src, size_t bytes)
     if (s->p.prec == LB_FP64) {
         LB_CUDA(s, cudaMemcpyAsync(s->f64[0], d, sizeof(double) * 9 * s->N, k, s->stream));
     } else {
-        const size_t gb = elem_size(s->p.prec) * 9 * (size_t)s->N;
+        const size_t gb = elem_size(s->p.prec) * (size_t)g_elems(s->p.nx, s->p.ny);
         LB_CUDA(s, cudaMemcpyAsync(s->g[0], d, gb, k, s->stream));
         LB_CUDA(s, cudaMemcpyAsync(s->dpsi[0], d + gb, sizeof(float) * s->N, k, s->stream));
     }

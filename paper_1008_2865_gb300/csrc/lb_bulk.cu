@@ -2,26 +2,26 @@
 // shared memory by the bulk-copy (TMA) engine: cp.async.bulk copies into
 // rings of row buffers, completion signalled through mbarrier transaction
 // counts, D rows ahead of the compute. The number of bytes in flight per SM is
-// then set by the rings in shared memory rather than by registers, which is
-// what a 25-point stencil streaming 80 bytes per site needs to keep HBM busy.
+// then set by the rings in shared memory rather than by registers.
 //
-// Geometry (T = float or __half, AE = 16 / sizeof(T) elements per 16 bytes):
-//   a CTA of BX threads owns TX = AE * floor((BX - 2) / AE) output columns
-//   (float: BX - 4) starting at x0 = blockIdx.x * TX (a multiple of AE), and marches
-//   over `rows` output rows. Thread k computes the collision at column
-//   x0 - 1 + k for k <= TX + 1 (the two halo columns included); the
-//   remaining threads repeat column TX + 1 without storing.
-//   Row unit j (j = 0, 1, ...) is {g* row y0 - 2 + j (all 9 populations,
-//   columns [x0 - AE, x0 + TX + AE)), dpsi row y0 + 1 + j (columns
-//   [x0 - 4, x0 + TX + 4))}; units -4..-1 carry only the dpsi rows
-//   y0 - 3 .. y0. Collision row r = y0 - 1 + it needs units up to it + 2.
-//   Periodic wrap in x splits a window into at most three aligned copies.
-// Schedule: units 0..D are issued before the first row; iteration it waits
-// for unit it+2 and, after the previous iteration's barrier, issues unit
-// it+1+D. A g* row is read by iterations j-2..j and a dpsi row by j..j+4, so
-// the slot a new unit overwrites was last read by iteration it-1 when
-// NG = D + 2 and NP = D + 6; the barrier it re-arms belongs to unit it,
-// waited at iteration it-2, when NB = D + 1.
+// Geometry (T = float or __half; nx a multiple of 32):
+//   a CTA of BX threads owns TX = 4 floor((BX - 2) / 4) output columns
+//   starting at x0 = blockIdx.x * TX (a multiple of 4, so every dpsi window
+//   starts on a 16-byte boundary) and marches over `rows` output rows.
+//   Thread k computes the collision at column x0 - 1 + k for k <= TX + 1 (the
+//   two halo columns included); the remaining threads repeat column TX + 1
+//   without storing.
+//   Row unit j (j = 0, 1, ...) is {the populations of row y0 - 1 + j: the
+//   whole 32-column tiles covering columns [x0 - 1, x0 + TX], contiguous in the
+//   tiled layout; dpsi row y0 + 1 + j, columns [x0 - 4, x0 + TX + 4)}; a
+//   leading unit carries the dpsi rows y0 - 3 .. y0. Collision row r = y0 - 1
+//   + it needs unit it. Periodic wrap in x splits a copy in two.
+// Schedule: units 0..D-1 are issued before the first row; iteration it waits
+// for unit it and, after the previous iteration's barrier, issues unit it+D.
+// A population row is read by its own iteration only and a dpsi row by five,
+// so the slot a new unit overwrites was last read by iteration it-1 when
+// NG = D + 1 and NP = D + 5; the barrier it re-arms belongs to unit it-1,
+// waited at iteration it-1, when NB = D + 1.
 //
 // Every wait on an mbarrier is bounded by a clock limit; a CTA whose wait
 // runs out sets the state's error flag and all its threads leave together at
@@ -121,44 +121,49 @@ __device__ __forceinline__ void copy_window(E* dst, const E* src, int xs, int w,
 
 template <typename T, int BX>
 struct BulkGeom {
-    static constexpr int AE = 16 / (int)sizeof(T);      // elements per 16 bytes
-    static constexpr int TX = ((BX - 2) / AE) * AE;     // output columns per CTA
-    static constexpr int WG = TX + 2 * AE;              // g* window width
-    static constexpr int WP = TX + 8;                   // dpsi window width
+    static constexpr int TX = ((BX - 2) / 4) * 4;          // output columns per CTA
+    static constexpr int KT = (TX + 64) / kTileW;          // tiles in a population window (max)
+    static constexpr int WG = KT * kTileElems;             // elements of a population window
+    static constexpr int WP = TX + 8;                      // dpsi window width
 };
 
 template <typename T, int BX, int D, bool REDUCE, bool OM1>
 __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
 {
     using G = BulkGeom<T, BX>;
-    constexpr int AE = G::AE, TX = G::TX, WG = G::WG, WP = G::WP;
-    constexpr int NG = D + 2, NP = D + 6, NB = D + 1;
+    constexpr int TX = G::TX, WG = G::WG, WP = G::WP;
+    constexpr int NG = D + 1, NP = D + 5, NB = D + 1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T* gring = reinterpret_cast<T*>(smem_raw);                                  // [NG][9][WG]
-    float* pring = reinterpret_cast<float*>(smem_raw + sizeof(T) * NG * 9 * WG); // [NP][WP]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * NG * 9 * WG +
-                                                 sizeof(float) * NP * WP);    // [NB + 1]
-    __shared__ float4 exR[2][BX + 2];
-    __shared__ float4 exL[2][BX + 2];
+    T* gring = reinterpret_cast<T*>(smem_raw);                                   // [NG][WG]
+    float* pring = reinterpret_cast<float*>(smem_raw + sizeof(T) * NG * WG);     // [NP][WP]
+    uint64_t* bars =
+        reinterpret_cast<uint64_t*>(smem_raw + sizeof(T) * NG * WG + sizeof(float) * NP * WP);
+    __shared__ float4 exR[2][BX + 2];        // right-moving f*: speeds 8, 1, 5
+    __shared__ float4 exL[2][BX + 2];        // left-moving f*: speeds 7, 3, 6
 
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
-    const int N = (int)a.N;
+    const int P = a.pitch;
+    const int ntile = nx / kTileW;               // tiles per row
     const int x0 = blockIdx.x * TX;
     const int y0 = blockIdx.y * a.rows;
     const int y1 = min(y0 + a.rows, ny);
     const int H = y1 - y0;
-    const int last_unit = H + 3;                 // units 0..H+3 are consumed
+    const int last_unit = H + 1;                 // units 0..H+1 are consumed
     const int txe = min(TX, nx - x0);
     const bool out_col = tid >= 1 && tid <= txe;
-    const int tcol = min(tid, TX + 1);
-    const int gpos = tcol + AE - 1;              // thread column in the g* window
-    const int ppos = tcol + 3;                   // thread column in the dpsi window
+    const int xu = x0 - 1 + min(tid, TX + 1);    // thread column, unwrapped (-1 .. nx)
+    const int ta = (x0 - 1) >> 5;                // first tile of the window, unwrapped
+    const int nt = ((x0 + TX) >> 5) - ta + 1;    // tiles in this CTA's window
+    const int gpos = ((xu >> 5) - ta) * kTileElems + (xu & (kTileW - 1));
+    const int ppos = min(tid, TX + 1) + 3;       // thread column in the dpsi window
     const int xc = x0 - 1 + tid;                 // output column (out_col threads)
+    const int cx = tcol(xc);
     const long long limit = a.wait_cycles;
-    const uint32_t unit_bytes = (uint32_t)(9 * WG * sizeof(T) + WP * sizeof(float)) + a.extra_tx;
+    const uint32_t unit_bytes =
+        (uint32_t)(nt * kTileElems * sizeof(T) + WP * sizeof(float)) + a.extra_tx;
 
-    // ---- producer: lanes 0..9 of warp 0 issue the copies of one unit
+    // ---- producer: lanes 0..2 of warp 0 issue the copies of one unit
     auto issue_unit = [&](int j) {
         const int lane = tid;                    // only called by warp 0
         uint64_t* bar = &bars[j < 0 ? NB : j % NB];
@@ -168,18 +173,19 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
         }
         __syncwarp();
         if (j < 0) {
-            // the four leading dpsi rows y0-3 .. y0 (units -4 .. -1)
+            // the four leading dpsi rows y0-3 .. y0
             if (lane < 4) {
                 const int q = wrapi(y0 - 3 + lane, ny);
-                copy_window(pring + (lane % NP) * WP, a.dpsi_in + q * nx, x0 - 4, WP, nx, bar);
+                copy_window(pring + lane * WP, a.dpsi_in + q * nx, x0 - 4, WP, nx, bar);
             }
             return;
         }
-        if (lane < 9) {
-            const int s = wrapi(y0 - 2 + j, ny);
-            copy_window(gring + ((j % NG) * 9 + lane) * WG, a.g_in + (lane * N + s * nx),
-                        x0 - AE, WG, nx, bar);
-        } else if (lane == 9) {
+        if (lane == 0) {
+            // whole tiles ta .. ta+nt-1 of population row y0-1+j, wrapped at the row ends
+            const T* row = a.g_in + wrapi(y0 - 1 + j, ny) * P;
+            T* dst = gring + (j % NG) * WG;
+            copy_window(dst, row, ta * kTileElems, nt * kTileElems, ntile * kTileElems, bar);
+        } else if (lane == 1) {
             const int q = wrapi(y0 + 1 + j, ny);
             copy_window(pring + ((j + 4) % NP) * WP, a.dpsi_in + q * nx, x0 - 4, WP, nx, bar);
         }
@@ -192,47 +198,31 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
     __syncthreads();
     if (tid < 32) {
         issue_unit(-1);
-        for (int j = 0; j <= D && j <= last_unit; ++j) issue_unit(j);
+        for (int j = 0; j < D && j <= last_unit; ++j) issue_unit(j);
     }
-
-    // the leading dpsi rows and units 0, 1 (g* rows y0-2, y0-1) before the first row;
-    // the barrier after the waits lets iterations 0 and 1 re-arm those barriers
-    bool fail = !mbar_wait_bounded(&bars[NB], 0, limit);
-    fail |= !mbar_wait_bounded(&bars[0], 0, limit);
-    fail |= !mbar_wait_bounded(&bars[1], 0, limit);
-    __syncthreads();
+    bool fail = !mbar_wait_bounded(&bars[NB], 0, limit);   // the leading dpsi rows
 
     float acc_m = 0.f, acc_0 = 0.f;
     float es = 0.f, em = 0.f, eb = 0.f, ms = 0.f;
     double d_es = 0.0, d_em = 0.0, d_eb = 0.0, d_ms = 0.0;
+    // population row offsets (row * P) of rows r-1, r, r+1 for the stores
+    int s0 = wrapi(y0 - 2, ny) * P;
+    int s1 = wrapi(y0 - 1, ny) * P;
+    int s2 = wrapi(y0, ny) * P;
 
     for (int it = 0; it <= H + 1; ++it) {
         const int r = y0 - 1 + it;
-        // ---- keep D units in flight (slots freed by the previous iteration's barrier);
-        // a barrier is re-armed only after warp 0 has seen its previous phase complete
-        if (tid < 32 && it + 1 + D <= last_unit && !__any_sync(0xffffffffu, fail)) {
+        // ---- keep D units in flight (slots freed by the previous iteration's barrier)
+        if (tid < 32 && it + D <= last_unit && !__any_sync(0xffffffffu, fail)) {
             fence_proxy_async_smem();
-            issue_unit(it + 1 + D);
+            issue_unit(it + D);
         }
-        // ---- unit it+2 completes rows r+1 (g*) and r+4 (dpsi)
-        {
-            const int j = it + 2;
-            fail |= !mbar_wait_bounded(&bars[j % NB], (uint32_t)((j / NB) & 1), limit);
-        }
-        // ---- pull f_i(x, r) = f*_i(x - c_i) from the g* ring (rows r-1, r, r+1)
-        const T* gm = gring + (it % NG) * 9 * WG + gpos;          // row r - 1
-        const T* gc = gring + ((it + 1) % NG) * 9 * WG + gpos;    // row r
-        const T* gp = gring + ((it + 2) % NG) * 9 * WG + gpos;    // row r + 1
+        // ---- unit it completes population row r and dpsi row r+2
+        fail |= !mbar_wait_bounded(&bars[it % NB], (uint32_t)((it / NB) & 1), limit);
+        const T* gr = gring + (it % NG) * WG + gpos;
         float f[9];
-        f[0] = lds_(gc);
-        f[1] = lds_(gc + WG - 1);
-        f[2] = lds_(gm + 2 * WG);
-        f[3] = lds_(gc + 3 * WG + 1);
-        f[4] = lds_(gp + 4 * WG);
-        f[5] = lds_(gm + 5 * WG - 1);
-        f[6] = lds_(gm + 6 * WG + 1);
-        f[7] = lds_(gp + 7 * WG + 1);
-        f[8] = lds_(gp + 8 * WG - 1);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = lds_(gr + kTileW * i);
         // ---- dpsi rows r-2 .. r+2 (ring slots it .. it+4)
         const float* rows[5];
 #pragma unroll
@@ -243,39 +233,61 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
         float gs[9];
         const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
 
-        if (out_col && r >= y0 && r < y1) {
-            T* o = a.g_out + (r * nx + xc);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) st_(o + i * N, gs[i]);
-            if (REDUCE) {
-                energy_site(rows, pc, a, es, em, eb);
-                ms += d;
-                if (((r - y0) & 15) == 15) {
-                    d_es += es; d_em += em; d_eb += eb; d_ms += ms;
-                    es = em = eb = ms = 0.f;
-                }
+        const bool out_site = out_col && r >= y0 && r < y1;
+        if (REDUCE && out_site) {
+            energy_site(rows, pc, a, es, em, eb);
+            ms += d;
+            if (((r - y0) & 15) == 15) {
+                d_es += es; d_em += em; d_eb += eb; d_ms += ms;
+                es = em = eb = ms = 0.f;
             }
         }
-        // ---- hand post-collision values to the neighbouring columns
+        // ---- stream on chip (Eq. 1) as in lb_fp32.cu: own-column speeds now,
+        // the neighbouring columns' after the barrier
         exR[it & 1][tid + 1] = make_float4(gs[8], gs[1], gs[5], 0.f);
         exL[it & 1][tid + 1] = make_float4(gs[7], gs[3], gs[6], 0.f);
+        const bool st_m = out_col && r - 1 >= y0;
+        const bool st_0 = out_site;
+        const bool st_p = out_col && r + 1 < y1;
         if (__syncthreads_or(fail)) {
             if (tid == 0) atomicOr(a.err, 1);
             // bounded wait for every unit this CTA issued and has not consumed
             if (tid == 0) {
-                for (int j = it + 3; j <= it + 1 + D && j <= last_unit; ++j)
+                for (int j = it + 1; j <= it + D && j <= last_unit; ++j)
                     mbar_wait_bounded(&bars[j % NB], (uint32_t)((j / NB) & 1), limit);
             }
             return;
         }
         const float4 R = exR[it & 1][tid];
         const float4 L = exL[it & 1][tid + 2];
+        if (st_m) {
+            T* o = a.g_out + (s0 + cx);
+            st_(o + kTileW * 4, gs[4]);
+            st_(o + kTileW * 7, L.x);
+            st_(o + kTileW * 8, R.x);
+        }
+        if (st_0) {
+            T* o = a.g_out + (s1 + cx);
+            st_(o, gs[0]);
+            st_(o + kTileW * 1, R.y);
+            st_(o + kTileW * 3, L.y);
+        }
+        if (st_p) {
+            T* o = a.g_out + (s2 + cx);
+            st_(o + kTileW * 2, gs[2]);
+            st_(o + kTileW * 5, R.z);
+            st_(o + kTileW * 6, L.z);
+        }
         acc_m += gs[4] + (R.x + L.x);
         acc_0 += gs[0] + (R.y + L.y);
         const float acc_p = gs[2] + (R.z + L.z);
-        if (out_col && r - 1 >= y0) a.dpsi_out[(r - 1) * nx + xc] = dpsi_of(acc_m, a);
+        if (st_m) a.dpsi_out[(r - 1) * nx + xc] = dpsi_of(acc_m, a);
         acc_m = acc_0;
         acc_0 = acc_p;
+        s0 = s1;
+        s1 = s2;
+        s2 += P;
+        if (s2 == a.npitch) s2 = 0;
     }
 
     if (REDUCE) {
@@ -293,8 +305,8 @@ template <typename T, int BX, int D, bool REDUCE, bool OM1>
 cudaError_t launch_bulk(const StepArgs<T>& a, int rows, cudaStream_t s)
 {
     using G = BulkGeom<T, BX>;
-    constexpr int NG = D + 2, NP = D + 6, NB = D + 1;
-    const size_t smem = sizeof(T) * NG * 9 * G::WG + sizeof(float) * NP * G::WP +
+    constexpr int NG = D + 1, NP = D + 5, NB = D + 1;
+    const size_t smem = sizeof(T) * NG * G::WG + sizeof(float) * NP * G::WP +
                         sizeof(uint64_t) * (NB + 1);
     auto kern = k_step_bulk<T, BX, D, REDUCE, OM1>;
     // the dynamic shared memory opt-in is a per-device function attribute
@@ -347,28 +359,16 @@ int bulk_tx(int block_x)
     }
 }
 
-template <typename T>
-int bulk_wg(int block_x)
-{
-    switch (block_x) {
-    case 64: return BulkGeom<T, 64>::WG;
-    case 128: return BulkGeom<T, 128>::WG;
-    case 256: return BulkGeom<T, 256>::WG;
-    default: return 0;
-    }
-}
-
 }  // namespace
 
 bool bulk_supported(int nx, int ny, int elem_bytes, int block_x)
 {
     (void)ny;
-    const int ae = 16 / elem_bytes;
     const int tx = elem_bytes == 2 ? bulk_tx<__half>(block_x) : bulk_tx<float>(block_x);
-    const int wg = elem_bytes == 2 ? bulk_wg<__half>(block_x) : bulk_wg<float>(block_x);
     if (tx <= 0) return false;
-    // every row and population plane starts on a 16-byte boundary, windows wrap at most once
-    return nx % ae == 0 && nx % 4 == 0 && nx >= wg && nx >= tx + 8;
+    // rows of whole tiles (every copy starts on a 16-byte boundary); a window
+    // of tiles and a dpsi window wrap at most once
+    return nx % kTileW == 0 && nx >= tx + 64;
 }
 
 int bulk_grid_blocks(int nx, int ny, int elem_bytes, Fp32Launch L)

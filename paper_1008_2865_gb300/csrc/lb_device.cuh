@@ -21,6 +21,18 @@ __device__ __forceinline__ int wrapi(int a, int n)
     return a < 0 ? a + n : a;
 }
 
+// Offset of column x within a row of the tiled population layout (lb_internal.h):
+// population i of site (x, y) is at y * pitch + tcol(x) + 32 i.
+__device__ __forceinline__ int tcol(int x) { return (x >> 5) * kTileElems + (x & (kTileW - 1)); }
+
+// The 9 populations of one site, p = g + y * pitch + tcol(x).
+template <typename T>
+__device__ __forceinline__ void load_site(float f[9], const T* __restrict__ p)
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = ldg_(p + kTileW * i);
+}
+
 // Two-belt force sums of Eq. FORCE in pair form. r[k] points at the stencil
 // centre's column in the dpsi row y + k - 2 (k = 0..4), so r[k][dx] is
 // dpsi(x + dx, y + k - 2). Returns S = sum_c K_c c dpsi(x + c), grouped by

@@ -2,29 +2,31 @@
 // Boltzmann method (Chibbaro et al., arXiv:1008.2865) for sm_103a, with the
 // populations stored as deviations from the rest equilibrium at rho_ref.
 //
-// State between steps: g*(t-1) = post-collision deviations f*_i - w_i rho_ref
-// (SoA [9][ny][nx]) and dpsi(t) = psi(rho(t)) - psi(rho_ref) ([ny][nx]).
-// One launch advances t -> t+1 and moves ~80 bytes per site in FP32:
-// 36 B of g* read, 36 B written, 4 B of dpsi read, 4 B written.
+// State between steps: g(t) = f(t) - w rho_ref, the streamed populations of
+// state t at their own site (tiled layout, lb_internal.h), and dpsi(t) =
+// psi(rho(t)) - psi(rho_ref) ([ny][nx]). One launch advances t -> t+1 and
+// moves ~80 bytes per site in FP32: 36 B of g read, 36 B written, 4 B of dpsi
+// read, 4 B written.
 //
 // Work decomposition. A CTA of BX threads owns a strip of BX-2 output
 // columns and `rows` output rows; thread k sits on column x0-1+k, so the two
 // edge threads are the one-column halo whose collisions the interior needs.
 // The CTA marches down its rows. For collision row r it
-//   1. pulls f_i(x, r) = f*_i(x - c_i, r) from global memory (Eq. 1 streaming,
-//      periodic) — the loads of row r+1 are issued before row r is computed;
+//   1. reads the 9 populations f_i(x, r) of its own site (one base address,
+//      immediate offsets) — the loads of row r+1 are issued before row r is
+//      computed;
 //   2. forms rho, j (Eqs. 2-3) and reads psi(t) of the 25-site stencil from a
 //      ring of 8 dpsi rows kept in shared memory (each dpsi row is read from
 //      HBM once per CTA);
 //   3. evaluates the two-belt force of Eq. FORCE in pair form, grouped by
 //      |c|^2 (the constant psi_ref cancels in every antisymmetric pair);
-//   4. relaxes towards the Eq. 4 equilibrium at u + F/(omega rho) and stores
-//      g*(t) for its own column;
-//   5. hands its three right-moving and three left-moving post-collision
-//      values to the neighbouring threads through shared memory, so that
-//      every thread accumulates rho(t+1) = sum_i f*_i(x - c_i) of rows r-1,
-//      r, r+1 in three rolling registers; row r-1 is then complete and its
-//      dpsi(t+1) is written.
+//   4. relaxes towards the Eq. 4 equilibrium at u + F/(omega rho);
+//   5. streams the post-collision values on chip (Eq. 1): the three
+//      right-moving and three left-moving values go to the neighbouring
+//      threads through shared memory, and every thread stores f(t+1) of its
+//      own column — the speeds with c_y = -1, 0, +1 into rows r-1, r, r+1.
+//      The same values summed in three rolling registers give rho(t+1) of
+//      rows r-1, r, r+1; row r-1 is then complete and its dpsi(t+1) is written.
 // One __syncthreads per row orders the exchange and the ring updates.
 // REDUCE launches also accumulate mass and the Sec. 5 pseudo-energies of
 // state t (FP32 per thread for 16 rows, then FP64), reduce them per CTA in
@@ -39,40 +41,6 @@ namespace {
 
 using namespace dev;
 
-// Pull f_i(x, r) = f*_i(x - c_i, r - c_iy) for the 9 D2Q9 speeds in the order
-// (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
-template <typename T>
-__device__ __forceinline__ void pull(float f[9], const T* __restrict__ g, long long N,
-                                     long long om, long long oc, long long op, int xm, int xc,
-                                     int xp)
-{
-    f[0] = ldg_(g + oc + xc);
-    f[1] = ldg_(g + N + oc + xm);
-    f[2] = ldg_(g + 2 * N + om + xc);
-    f[3] = ldg_(g + 3 * N + oc + xp);
-    f[4] = ldg_(g + 4 * N + op + xc);
-    f[5] = ldg_(g + 5 * N + om + xm);
-    f[6] = ldg_(g + 6 * N + om + xp);
-    f[7] = ldg_(g + 7 * N + op + xp);
-    f[8] = ldg_(g + 8 * N + op + xm);
-}
-
-// The same pull with 32-bit element offsets (9 N < 2^31 is enforced at init).
-template <typename T>
-__device__ __forceinline__ void pull32(float f[9], const T* __restrict__ g, int N, int om, int oc,
-                                       int op, int xm, int xc, int xp)
-{
-    f[0] = ldg_(g + (oc + xc));
-    f[1] = ldg_(g + (N + oc + xm));
-    f[2] = ldg_(g + (2 * N + om + xc));
-    f[3] = ldg_(g + (3 * N + oc + xp));
-    f[4] = ldg_(g + (4 * N + op + xc));
-    f[5] = ldg_(g + (5 * N + om + xm));
-    f[6] = ldg_(g + (6 * N + om + xp));
-    f[7] = ldg_(g + (7 * N + op + xp));
-    f[8] = ldg_(g + (8 * N + op + xm));
-}
-
 // Advance a row offset (row * nx) by one row with periodic wrap.
 __device__ __forceinline__ int next_row(int off, int nx, int N)
 {
@@ -80,13 +48,13 @@ __device__ __forceinline__ int next_row(int off, int nx, int N)
     return off == N ? 0 : off;
 }
 
-// Resident warps per SM the register budget is cut for: the plain omega = 1 step
-// fits 48 warps (40 registers) in CTAs of 128 threads or more, the other plain
-// steps 40 warps and the reduction step 32 warps, all without spills. The step
-// is bound by the latency of its global loads, so occupancy is throughput here.
+// Resident warps per SM the register budget is cut for: 40 warps (48 registers)
+// for the plain steps and 32 warps (64 registers) for the reduction step, the
+// most that compile without spills (48 warps at 40 registers spill, and run
+// slower). The step is bound by the latency of its global loads.
 template <int BX, bool REDUCE, bool OM1>
 struct StepWarps {
-    static constexpr int value = REDUCE ? 32 : ((OM1 && BX >= 128) ? 48 : 40);
+    static constexpr int value = REDUCE ? 32 : 40;
 };
 
 // One CTA's tile of the step: output columns [bx (BX-2), +BX-2) and output
@@ -97,39 +65,37 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
 {
     constexpr int W = BX + 4;
     __shared__ float win[8][W];              // dpsi(t) rows, slot = row & 7
-    __shared__ float4 exR[2][BX + 2];        // right-moving f*: (cy=-1, 0, +1)
-    __shared__ float4 exL[2][BX + 2];        // left-moving f*
+    __shared__ float4 exR[2][BX + 2];        // right-moving f*: speeds 8, 1, 5 (cy = -1, 0, +1)
+    __shared__ float4 exL[2][BX + 2];        // left-moving f*: speeds 7, 3, 6
 
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
     const int N = (int)a.N;
+    const int P = a.pitch, NP = a.npitch;
     const int x0 = bx * (BX - 2);
     const int y0 = by * a.rows;
     const int y1 = min(y0 + a.rows, ny);
     const int txe = min(BX - 2, nx - x0);
     const bool out_col = tid >= 1 && tid <= txe;
     const int xc = wrapi(x0 - 1 + tid, nx);
-    const int xm = xc == 0 ? nx - 1 : xc - 1;
-    const int xp = xc == nx - 1 ? 0 : xc + 1;
     const int pc0 = wrapi(x0 - 3 + tid, nx);
     const int pc1 = wrapi(x0 - 3 + BX + (tid & 3), nx);
+    const int cx = tcol(xc);
 
-    // dpsi rows y0-3 .. y0+1 into the ring
     for (int rr = y0 - 3; rr <= y0 + 1; ++rr) {
         const float* src = a.dpsi_in + wrapi(rr, ny) * nx;
         win[rr & 7][tid] = __ldg(src + pc0);
         if (tid < 4) win[rr & 7][BX + tid] = __ldg(src + pc1);
     }
-    // Row offsets (row * nx, periodic) kept incrementally, no division in the
-    // loop: at the top of iteration r, o0, o1, o2 hold rows r-1, r, r+1 and oq
-    // holds row r+3 (the dpsi row prefetched into the ring).
-    int o0 = wrapi(y0 - 2, ny) * nx;
-    int o1 = wrapi(y0 - 1, ny) * nx;
-    int o2 = wrapi(y0, ny) * nx;
+    // Row offsets (row * P) of g, periodic, kept incrementally: at the top of
+    // iteration r, s0, s1, s2 hold rows r-1, r, r+1 and oq the dpsi row r+3.
+    int s0 = wrapi(y0 - 2, ny) * P;
+    int s1 = wrapi(y0 - 1, ny) * P;
+    int s2 = wrapi(y0, ny) * P;
     int oq = wrapi(y0 + 2, ny) * nx;
 
     float f[9];
-    pull32(f, a.g_in, N, o0, o1, o2, xm, xc, xp);   // collision row y0 - 1
+    load_site(f, a.g_in + (s1 + cx));                  // collision row y0 - 1
     __syncthreads();
 
     float acc_m = 0.f, acc_0 = 0.f;
@@ -137,7 +103,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
     double d_es = 0.0, d_em = 0.0, d_eb = 0.0, d_ms = 0.0;
 
     for (int r = y0 - 1; r <= y1; ++r) {
-        // ---- prefetch: dpsi row r+3 and the pulled populations of row r+1
+        // ---- prefetch: dpsi row r+3 and the populations of row r+1
         const bool need_psi = r <= y1 - 1;
         float pn0 = 0.f, pn1 = 0.f;
         if (need_psi) {
@@ -146,12 +112,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
             if (tid < 4) pn1 = __ldg(src + pc1);
         }
         oq = next_row(oq, nx, N);
-        // rows r, r+1, r+2: the pull of collision row r+1
-        o0 = o1;
-        o1 = o2;
-        o2 = next_row(o2, nx, N);
         float fn[9];
-        if (r < y1) pull32(fn, a.g_in, N, o0, o1, o2, xm, xc, xp);
+        if (r < y1) load_site(fn, a.g_in + (s2 + cx));
 
         // ---- force from the dpsi(t) ring, then moments and collision
         const float* rows[5];
@@ -164,12 +126,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
         const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
 
         const bool out_site = out_col && r >= y0 && r < y1;
-        if (out_site) {
-            T* o = a.g_out + (r * nx + xc);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) st_(o + i * N, gs[i]);
-            if (REDUCE) ms += d;
-        }
+        if (REDUCE && out_site) ms += d;
 
         // ---- exchange post-collision values with the neighbouring columns
         exR[r & 1][tid + 1] = make_float4(gs[8], gs[1], gs[5], 0.f);
@@ -178,15 +135,47 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
             win[(r + 3) & 7][tid] = pn0;
             if (tid < 4) win[(r + 3) & 7][BX + tid] = pn1;
         }
+        // ---- f(t+1) = f*(x - c_i) (Eq. 1) for the own column: the speeds with
+        // c_y = -1, 0, +1 land in rows r-1, r, r+1. The own-column speeds 4, 0, 2
+        // are stored now, the six from the neighbouring columns after the barrier.
+        const bool st_m = out_col && r - 1 >= y0;
+        const bool st_0 = out_site;
+        const bool st_p = out_col && r + 1 < y1;
+        if (st_m) st_(a.g_out + (s0 + cx) + kTileW * 4, gs[4]);
+        if (st_0) st_(a.g_out + (s1 + cx), gs[0]);
+        if (st_p) st_(a.g_out + (s2 + cx) + kTileW * 2, gs[2]);
+        acc_m += gs[4];
+        acc_0 += gs[0];
+        float acc_p = gs[2];
         __syncthreads();
         const float4 R = exR[r & 1][tid];       // from column x-1
         const float4 L = exL[r & 1][tid + 2];   // from column x+1
-        acc_m += gs[4] + (R.x + L.x);
-        acc_0 += gs[0] + (R.y + L.y);
-        const float acc_p = gs[2] + (R.z + L.z);
-        if (out_col && r - 1 >= y0) a.dpsi_out[(r - 1) * nx + xc] = dpsi_of(acc_m, a);
+        if (st_m) {
+            T* o = a.g_out + (s0 + cx);
+            st_(o + kTileW * 7, L.x);
+            st_(o + kTileW * 8, R.x);
+        }
+        if (st_0) {
+            T* o = a.g_out + (s1 + cx);
+            st_(o + kTileW * 1, R.y);
+            st_(o + kTileW * 3, L.y);
+        }
+        if (st_p) {
+            T* o = a.g_out + (s2 + cx);
+            st_(o + kTileW * 5, R.z);
+            st_(o + kTileW * 6, L.z);
+        }
+        acc_m += R.x + L.x;
+        acc_0 += R.y + L.y;
+        acc_p += R.z + L.z;
+        // rho(t+1) of row r-1 is complete
+        if (st_m) a.dpsi_out[(r - 1) * nx + xc] = dpsi_of(acc_m, a);
         acc_m = acc_0;
         acc_0 = acc_p;
+        s0 = s1;
+        s1 = s2;
+        s2 += P;
+        if (s2 == NP) s2 = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fn[i];
         if (REDUCE && out_site) {
@@ -287,21 +276,19 @@ __global__ void k_delta_init(T* __restrict__ g, float* __restrict__ dpsi,
                              double rho0)
 {
     const long long N = (long long)nx * ny;
+    const int pitch = g_pitch(nx);
     const double w[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
                          1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
-    const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const double cpsi = -sqrt(rho0) * exp(-rho_ref / rho0);
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
          s += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(s / nx), x = (int)(s % nx);
-        // f*_i(x) such that the first pull gives f_i(x, 0) = w_i rho_init(x)
+        // f_i(x, 0) = w_i rho_init(x): the fluid at rest
+        T* p = g + (long long)y * pitch + tcol(x);
+        const double d = rho[s] - rho_ref;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const long long src = (long long)wrapi(y + cy[i], ny) * nx + wrapi(x + cx[i], nx);
-            st_(g + i * N + s, (float)(w[i] * (rho[src] - rho_ref)));
-        }
-        dpsi[s] = (float)cpsi * expm1f((float)(-(rho[s] - rho_ref) / rho0));
+        for (int i = 0; i < 9; ++i) st_(p + kTileW * i, (float)(w[i] * d));
+        dpsi[s] = (float)cpsi * expm1f((float)(-d / rho0));
     }
 }
 
@@ -311,15 +298,12 @@ __global__ void k_delta_fields(const T* __restrict__ g, int nx, int ny, double r
                                double* __restrict__ uy)
 {
     const long long N = (long long)nx * ny;
+    const int pitch = g_pitch(nx);
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
          s += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(s / nx), x = (int)(s % nx);
-        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-        const long long om = (long long)(y == 0 ? ny - 1 : y - 1) * nx;
-        const long long oc = (long long)y * nx;
-        const long long op = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
         float f[9];
-        pull(f, g, N, om, oc, op, xm, x, xp);
+        load_site(f, g + (long long)y * pitch + tcol(x));
         double d = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) d += (double)f[i];
@@ -359,11 +343,8 @@ __global__ void __launch_bounds__(256) k_delta_energy(const T* __restrict__ g,
         v[0] += 0.5 * pc * b1;
         v[1] += 0.5 * pc * b2;
         v[2] += (double)a.half_A1 * pc * pc;
-        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-        const long long om = (long long)(y == 0 ? ny - 1 : y - 1) * nx;
-        const long long op = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
         float f[9];
-        pull(f, g, N, om, (long long)y * nx, op, xm, x, xp);
+        load_site(f, g + (long long)y * a.pitch + tcol(x));
         double d = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) d += (double)f[i];

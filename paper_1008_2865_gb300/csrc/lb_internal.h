@@ -24,16 +24,30 @@ struct Couplings {
 };
 Couplings couplings(double G1, double G2);
 
+// Populations of an FP32 / FP16 state ("tiled" layout): rows of 32-column
+// tiles, each tile holding the 9 populations of its 32 sites one after the
+// other, so that element (i, x, y) sits at
+//   y * g_pitch(nx) + (x / 32) * 288 + 32 i + x % 32.
+// A warp reading the 9 populations of 32 consecutive sites makes 9 contiguous
+// 128-byte requests from one base address (immediate offsets). Columns past
+// nx in the last tile of a row are padding (zero, never read by a step).
+constexpr int kTileW = 32;
+constexpr int kTileElems = 9 * kTileW;
+__host__ __device__ inline int g_pitch(int nx) { return kTileElems * ((nx + kTileW - 1) / kTileW); }
+__host__ __device__ inline long long g_elems(int nx, int ny) { return (long long)ny * g_pitch(nx); }
+
 // Arguments of the fused FP32 step (deviation storage, see lb.h LB_FP32).
 template <typename T>
 struct StepArgs {
-    const T* __restrict__ g_in;      // [9][ny][nx] post-collision deviations of state t-1
-    T* __restrict__ g_out;           // [9][ny][nx] post-collision deviations of state t
+    const T* __restrict__ g_in;      // tiled f(t) - w rho_ref: populations of state t
+    T* __restrict__ g_out;           // tiled f(t+1) - w rho_ref
     const float* __restrict__ dpsi_in;   // [ny][nx] psi(t) - psi_ref
     float* __restrict__ dpsi_out;        // [ny][nx] psi(t+1) - psi_ref
     int nx, ny;
     int rows;                        // output rows per CTA
     long long N;                     // nx*ny
+    int pitch;                       // g_pitch(nx): elements per row of g
+    int npitch;                      // g_elems(nx, ny): elements per g buffer
     float omega, omc, inv_omega;     // omega, 1-omega, 1/omega
     float w0, w1, w2;                // D2Q9 weights
     float K1, K2, K4, K5, K8;        // force couplings
@@ -55,7 +69,7 @@ struct StepArgs {
 struct Fp32Launch {
     int block_x;   // threads per CTA
     int rows;      // output rows per CTA
-    int pipeline;  // 0: register-prefetch pull (any shape), 1: bulk-copy rings (aligned shapes)
+    int pipeline;  // 0: register prefetch (any shape), 1: bulk-copy rings (nx % 32 == 0)
 };
 int fp32_grid_blocks(int nx, int ny, Fp32Launch L);
 cudaError_t fp32_step(const StepArgs<float>& a, Fp32Launch L, bool reduce, cudaStream_t s);
@@ -135,7 +149,7 @@ struct lb_state {
     long long t = 0;
     bool poisoned = false;
     long long N = 0;
-    // FP32 / FP16 deviation storage
+    // FP32 / FP16 deviation storage (g tiled, lbsc::g_elems elements each)
     void* g[2] = {nullptr, nullptr};
     float* dpsi[2] = {nullptr, nullptr};
     int cur = 0;

@@ -107,8 +107,8 @@ def test_fp32_parity(nx, ny, G2, omega, mode, seed, steps):
 
 @pytest.mark.parametrize("nx,launch", [(301, (64, 16, 0)), (301, (96, 17, 0)), (301, (128, 16, 0)),
                                        (301, (192, 40, 0)), (301, (256, 33, 0)),
-                                       (300, (64, 16, 1)), (300, (128, 23, 1)),
-                                       (300, (256, 40, 1)), (512, (128, 64, 1))])
+                                       (320, (64, 16, 1)), (320, (128, 23, 1)),
+                                       (320, (256, 40, 1)), (512, (128, 64, 1))])
 def test_fp32_launch_shapes_agree(nx, launch):
     """Every CTA shape and both pipelines give the trajectory of the oracle (tile edges,
     halo columns, ragged strips and row chunks, periodic wrap of the copy windows)."""
@@ -262,10 +262,10 @@ def test_pipeline_availability():
         assert lat.launch == (128, 32, 1)
     with Lattice(inputs.noisy_density(301, 64, seed=1)) as lat:
         with pytest.raises(LBError):
-            lat.set_launch(128, 32, 1)             # odd width: no 16-byte row alignment
+            lat.set_launch(128, 32, 1)             # not a whole number of 32-column tiles
     with Lattice(inputs.noisy_density(516, 64, seed=1), prec="fp16_delta") as lat:
         with pytest.raises(LBError):
-            lat.set_launch(128, 32, 1)             # fp16 rows need 8-element alignment
+            lat.set_launch(128, 32, 1)             # 516 = 16 tiles + 4 columns
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
