@@ -1,8 +1,10 @@
 // lb_bulk.cu — the fused step of lb_fp32.cu with its input rows staged in
 // shared memory by the bulk-copy (TMA) engine: cp.async.bulk copies into
 // rings of row buffers, completion signalled through mbarrier transaction
-// counts, D rows ahead of the compute. The number of bytes in flight per SM is
-// then set by the rings in shared memory rather than by registers.
+// counts, D rows ahead of the compute, so that the loads in flight do not
+// occupy registers. On GB300 the shallowest ring (D = 1) is the fastest: every
+// extra row of ring costs resident CTAs, and the step is bound by latency per
+// warp rather than by the depth of the prefetch.
 //
 // Geometry (T = float or __half; nx a multiple of 32):
 //   a CTA of BX threads owns TX = 4 floor((BX - 2) / 4) output columns
@@ -328,7 +330,7 @@ cudaError_t launch_bulk(const StepArgs<T>& a, int rows, cudaStream_t s)
 template <typename T, int BX>
 cudaError_t launch_bulk_bx(const StepArgs<T>& a, int rows, bool reduce, bool om1, cudaStream_t s)
 {
-    constexpr int D = 3;
+    constexpr int D = 1;   // 8192^2 at 128 x 48: D = 1, 2, 3, 4 -> 0.915, 0.965, 0.972, 1.077 ms
     if (reduce)
         return om1 ? launch_bulk<T, BX, D, true, true>(a, rows, s)
                    : launch_bulk<T, BX, D, true, false>(a, rows, s);
