@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 NX = NY = 8192
 G1, G2, OMEGA, SEED = -5.0, 0.6, 1.0, 7
 TRACE_EVERY = 10
-BYTES_PER_SITE = 80          # 36 B g* in + 36 B g* out + 4 B dpsi in + 4 B dpsi out
+BYTES_PER_SITE = 80          # 36 B populations in + 36 B out + 4 B dpsi in + 4 B dpsi out
 METRIC = "MLUPS and % HBM roofline (FP32 fused step, 1 GB300); adjoint+batched vs plain"
 WORKLOAD = ("{n}x{n} periodic D2Q9 two-belt Shan-Chen, FP32 (deviation storage), omega=1, "
             "G1=-5.0, G2=0.6, rho=0.7(1+-1%) seeded uniform noise (seed 7), energy+mass "

@@ -82,7 +82,7 @@ __device__ __forceinline__ void energy_site(const float* const r[5], float pc,
     eb = fmaf(a.half_A1 * pc, pc, eb);
 }
 
-// Moments (Eqs. 2-3) and BGK relaxation (Eq. 1) of the pulled deviations
+// Moments (Eqs. 2-3) and BGK relaxation (Eq. 1) of the deviations
 // f_i - w_i rho_ref towards the Eq. 4 equilibrium at u + F/(omega rho),
 // written as deviations again:
 //   g*_i = (1 - omega) g_i + omega w_i d + omega w_i rho (3 c.u + 9/2 (c.u)^2 - 3/2 u^2)
