@@ -132,7 +132,7 @@ lb_status lb_trace(lb_state* s, double* buf, int cap, int* count);
  *      multiple of 32 and nx >= block_x + 64).
  * lb_init starts with pipeline 0 (measured the faster of the two on GB300 for
  * the 8192 x 8192 lattice). rows_per_cta is in
- * [16, 4096]. The shape changes how the work is split, not the trajectory;
+ * [4, 4096]. The shape changes how the work is split, not the trajectory;
  * only the FP32 rounding of the energy partial sums depends on it.
  * Errors: LB_ERR_ARG for NULL or unsupported values, LB_ERR_STATE for an FP64
  * state (whose kernels have no such shape). */
@@ -223,7 +223,7 @@ lb_status lb_batch_energy(lb_batch* b, int replica, double out[4]);
 lb_status lb_batch_fields(lb_batch* b, int replica, double* rho, double* ux, double* uy);
 lb_status lb_batch_trace(lb_batch* b, int replica, double* buf, int cap, int* count);
 /* Tile shape shared by all replicas (block_x in {64, 96, 128, 192, 256},
- * rows_per_cta in [16, 4096]) and whether steps replay from a CUDA graph
+ * rows_per_cta in [4, 4096]) and whether steps replay from a CUDA graph
  * (use_graph 0 or 1). Defaults: 128, 32, 1. */
 lb_status lb_batch_get_launch(const lb_batch* b, int* block_x, int* rows_per_cta, int* use_graph);
 lb_status lb_batch_set_launch(lb_batch* b, int block_x, int rows_per_cta, int use_graph);

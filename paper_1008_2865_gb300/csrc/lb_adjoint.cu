@@ -38,23 +38,48 @@ namespace {
 
 constexpr int kAdjThreads = 256;
 
-__device__ __forceinline__ int wrp(int a, int n)
+// Periodic neighbourhood of site (x, y), computed once per site (nx, ny >= 5):
+// columns x-2 .. x+2 and row offsets (y-2 .. y+2) * nx.
+struct Nbr5 {
+    int xo[5];
+    int yo[5];
+};
+
+__device__ __forceinline__ Nbr5 nbr5(int x, int y, int nx, int ny)
 {
-    a %= n;
-    return a < 0 ? a + n : a;
+    Nbr5 n;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        int xx = x + k - 2, yy = y + k - 2;
+        xx += xx < 0 ? nx : 0;
+        xx -= xx >= nx ? nx : 0;
+        yy += yy < 0 ? ny : 0;
+        yy -= yy >= ny ? ny : 0;
+        n.xo[k] = xx;
+        n.yo[k] = yy * nx;
+    }
+    return n;
 }
 
-// The 5 x 5 neighbourhood of a periodic FP32 field around (x, y): v[k][m] =
-// field(x + m - 2, y + k - 2).
-__device__ __forceinline__ void gather5(const float* __restrict__ fld, int x, int y, int nx,
-                                        int ny, float v[5][5])
+// The 5 x 5 neighbourhood of a periodic FP32 field: v[k][m] = field(x + m - 2, y + k - 2).
+__device__ __forceinline__ void gather5(const float* __restrict__ fld, const Nbr5& nb,
+                                        float v[5][5])
 {
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        const float* row = fld + (long long)wrp(y + k - 2, ny) * nx;
 #pragma unroll
-        for (int m = 0; m < 5; ++m) v[k][m] = __ldg(row + wrp(x + m - 2, nx));
+        for (int m = 0; m < 5; ++m) v[k][m] = __ldg(fld + nb.yo[k] + nb.xo[m]);
     }
+}
+
+// D2Q9 speeds in the order of the populations (compile-time in unrolled loops).
+__host__ __device__ constexpr int cx_of(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy_of(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
 }
 
 // Deviations f_i(x, y) - w_i rho_ref of state t, read from the tiled populations.
@@ -63,9 +88,6 @@ __device__ __forceinline__ void site_f(const float* __restrict__ g, int pitch, i
 {
     load_site(f, g + y * pitch + tcol(x));
 }
-
-__constant__ int ACX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__constant__ int ACY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
 struct AdjArgs {
     StepArgs<float> a;        // couplings, weights, rho_ref, psi_ref, omega of the state
@@ -109,8 +131,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A)
         site_f(A.g, a.pitch, x, y, f);
         const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
         const float rho = a.rho_ref + d;
+        const Nbr5 nb = nbr5(x, y, nx, ny);
         float p[5][5];
-        gather5(A.dpsi, x, y, nx, ny, p);
+        gather5(A.dpsi, nb, p);
         const float pr = a.psi_ref;
         const float pc = pr + p[2][2];
         // class sums of psi (not deviations) around the site
@@ -152,8 +175,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
         const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
         const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
         const float rho = a.rho_ref + d;
+        const Nbr5 nb = nbr5(x, y, nx, ny);
         float p[5][5];
-        gather5(A.dpsi, x, y, nx, ny, p);
+        gather5(A.dpsi, nb, p);
         const float* rows[5] = {&p[0][2], &p[1][2], &p[2][2], &p[3][2], &p[4][2]};
         float Swx, Swy, Spx, Spy;
         force_sums(rows, A.aw, Swx, Swy);
@@ -167,14 +191,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
         float rb = 0.f, vbx = 0.f, vby = 0.f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const int xi = wrp(x + ACX[i], nx), yi = wrp(y + ACY[i], ny);
-            const float ls = __ldg(A.lam_next + i * N + yi * nx + xi);   // streamed back
-            const float cu = ACX[i] * vx + ACY[i] * vy;
+            const int ci = cx_of(i), cj = cy_of(i);
+            const float ls = __ldg(A.lam_next + i * N + nb.yo[2 + cj] + nb.xo[2 + ci]);   // streamed back
+            const float cu = ci * vx + cj * vy;
             const float feq = w[i] * rho * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * usq);
             rb += om * ls * feq * inv;
             const float k = om * ls * w[i] * rho;
-            vbx += k * (3.f * ACX[i] + 9.f * cu * ACX[i] - 3.f * vx);
-            vby += k * (3.f * ACY[i] + 9.f * cu * ACY[i] - 3.f * vy);
+            vbx += k * (3.f * ci + 9.f * cu * ci - 3.f * vx);
+            vby += k * (3.f * cj + 9.f * cu * cj - 3.f * vy);
         }
         const float Fbx = vbx * inv / om, Fby = vby * inv / om;
         rb -= (vbx * vx + vby * vy) * inv;
@@ -199,20 +223,21 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_b(const AdjArgs A)
     for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
         const int y = s / nx, x = s % nx;
         // sum_c K_c c . Q(y + c): the x part is the force stencil of Qx, the y part of Qy
+        const Nbr5 nb = nbr5(x, y, nx, ny);
         float q[5][5];
         const float* rows[5] = {&q[0][2], &q[1][2], &q[2][2], &q[3][2], &q[4][2]};
         float sx, sy, tx, ty;
-        gather5(A.Qx, x, y, nx, ny, q);
+        gather5(A.Qx, nb, q);
         force_sums(rows, a, sx, sy);
-        gather5(A.Qy, x, y, nx, ny, q);
+        gather5(A.Qy, nb, q);
         force_sums(rows, a, tx, ty);
         const float rb = A.rbar[s] + A.dpsidrho[s] * (sx + ty);
         const float jbx = A.jbx[s], jby = A.jby[s];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const int xi = wrp(x + ACX[i], nx), yi = wrp(y + ACY[i], ny);
-            const float ls = __ldg(A.lam_next + i * N + yi * nx + xi);
-            A.lam[i * N + s] = fmaf(omc, ls, rb + ACX[i] * jbx + ACY[i] * jby);
+            const int ci = cx_of(i), cj = cy_of(i);
+            const float ls = __ldg(A.lam_next + i * N + nb.yo[2 + cj] + nb.xo[2 + ci]);
+            A.lam[i * N + s] = fmaf(omc, ls, rb + ci * jbx + cj * jby);
         }
     }
 }

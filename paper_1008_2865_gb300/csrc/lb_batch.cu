@@ -281,7 +281,7 @@ lb_status lb_batch_set_launch(lb_batch* b, int block_x, int rows_per_cta, int us
     if (b->poisoned) return LB_ERR_STATE;
     if (block_x != 64 && block_x != 96 && block_x != 128 && block_x != 192 && block_x != 256)
         return LB_ERR_ARG;
-    if (rows_per_cta < 16 || rows_per_cta > 4096 || (use_graph != 0 && use_graph != 1))
+    if (rows_per_cta < kMinRows || rows_per_cta > kMaxRows || (use_graph != 0 && use_graph != 1))
         return LB_ERR_ARG;
     if (cudaSetDevice(b->device) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess)
         return poison(b);

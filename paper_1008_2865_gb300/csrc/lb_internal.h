@@ -65,6 +65,10 @@ struct StepArgs {
     unsigned int extra_tx;           // test hook: bytes a unit's barrier expects beyond its copies
 };
 
+// Output rows per CTA accepted by lb_set_launch / lb_batch_set_launch.
+constexpr int kMinRows = 4;
+constexpr int kMaxRows = 4096;
+
 // Launchers (lb_fp32.cu). All return the launch's cudaError_t.
 struct Fp32Launch {
     int block_x;   // threads per CTA

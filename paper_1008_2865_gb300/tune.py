@@ -19,7 +19,7 @@ import threading
 
 BLOCK_X = (64, 96, 128, 192, 256)
 BULK_BLOCK_X = (64, 128, 256)
-ROWS = (16, 24, 32, 48, 64, 96, 128, 192, 256, 384)
+ROWS = (4, 8, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384)
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_launch.json")
 _lock = threading.Lock()
 
@@ -131,7 +131,7 @@ def tune_batch(rho_list, G2_list, prec="fp32", steps=20, device=0, save=True, G1
     with Batch(rho_list, G1=G1, G2=list(G2_list), prec=prec, trace_every=10, device=device,
                stream=stream.cuda_stream) as b:
         for bx in BLOCK_X:
-            for rows in (16, 24, 32, 48, 64):
+            for rows in (8, 12, 16, 24, 32, 48, 64):
                 try:
                     b.set_launch(bx, rows, 1)
                 except Exception:

@@ -220,7 +220,7 @@ def test_step_arguments_and_time():
         with pytest.raises(LBError):
             lat.set_launch(100, 16, 0)
         with pytest.raises(LBError):
-            lat.set_launch(128, 8, 0)
+            lat.set_launch(128, 3, 0)
         with pytest.raises(LBError):
             lat.set_launch(128, 16, 1)      # nx = 16 is too narrow for the copy windows
         with pytest.raises(LBError):
