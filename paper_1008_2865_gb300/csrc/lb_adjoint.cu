@@ -94,7 +94,7 @@ struct AdjArgs {
     StepArgs<float> aw;       // couplings replaced by the D2Q9 weights (S_w)
     StepArgs<float> ap;       // couplings replaced by the E(8) weights (S_p)
     float G1, G2;
-    float sqrt_rho0;
+    float inv_sqrt_rho0;      // 1 / sqrt(rho0): psi'(rho) = exp(-rho/rho0) / sqrt(rho0)
     const float* g;           // tiled f(t) - w rho_ref
     const float* dpsi;        // dpsi(t)
     const float* lam_next;    // [9][N] dJ/df(t+1)
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A)
         const float sw = A.aw.K0 * pc + A.aw.K1 * S1 + A.aw.K2 * S2;
         const float sp = A.ap.K0 * pc + A.ap.K1 * S1 + A.ap.K2 * S2 + A.ap.K4 * S4 +
                          A.ap.K5 * S5 + A.ap.K8 * S8;
-        const float dpr = __expf(-rho * a.inv_rho0) / A.sqrt_rho0;
+        const float dpr = __expf(-rho * a.inv_rho0) * A.inv_sqrt_rho0;
         const double mis = (double)rho - A.rho_target[s];
         const float lam = dpr * dEdpsi + (float)(2.0 * mis);
 #pragma unroll
@@ -188,21 +188,26 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
         const float inv = 1.f / rho;
         const float vx = fmaf(Fx, a.inv_omega, jx) * inv, vy = fmaf(Fy, a.inv_omega, jy) * inv;
         const float usq = vx * vx + vy * vy;
+        // rho-bar gets omega sum_i l*_i feq_i / rho = omega sum_i l*_i w_i (1 + 3 c.v + ...);
+        // v-bar = omega rho sum_i l*_i w_i (3 c_i + 9 (c_i.v) c_i - 3 v)
         float rb = 0.f, vbx = 0.f, vby = 0.f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int ci = cx_of(i), cj = cy_of(i);
-            const float ls = __ldg(A.lam_next + i * N + nb.yo[2 + cj] + nb.xo[2 + ci]);   // streamed back
+            // l*_i(x) = l'_i(x + c_i): the adjoint streamed back
+            const float lw = w[i] * __ldg(A.lam_next + i * N + nb.yo[2 + cj] + nb.xo[2 + ci]);
             const float cu = ci * vx + cj * vy;
-            const float feq = w[i] * rho * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * usq);
-            rb += om * ls * feq * inv;
-            const float k = om * ls * w[i] * rho;
-            vbx += k * (3.f * ci + 9.f * cu * ci - 3.f * vx);
-            vby += k * (3.f * cj + 9.f * cu * cj - 3.f * vy);
+            rb += lw * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * usq);
+            const float t9 = 9.f * cu;
+            vbx += lw * (3.f * ci + t9 * ci - 3.f * vx);
+            vby += lw * (3.f * cj + t9 * cj - 3.f * vy);
         }
-        const float Fbx = vbx * inv / om, Fby = vby * inv / om;
+        rb *= om;
+        vbx *= om * rho;
+        vby *= om * rho;
+        const float Fbx = vbx * inv * a.inv_omega, Fby = vby * inv * a.inv_omega;
         rb -= (vbx * vx + vby * vy) * inv;
-        const float dpr = __expf(-rho * a.inv_rho0) / A.sqrt_rho0;
+        const float dpr = __expf(-rho * a.inv_rho0) * A.inv_sqrt_rho0;
         A.jbx[s] = vbx * inv;
         A.jby[s] = vby * inv;
         A.rbar[s] = rb + dpr * (-(Fbx * Sx + Fby * Sy));
@@ -370,7 +375,7 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
     A.ap = with_weights(A.a, true);
     A.G1 = (float)s->p.G1;
     A.G2 = (float)s->p.G2;
-    A.sqrt_rho0 = (float)std::sqrt(s->p.rho0);
+    A.inv_sqrt_rho0 = (float)(1.0 / std::sqrt(s->p.rho0));
     A.rho_target = tgt;
     A.partials = part;
     A.counter = cnt;
