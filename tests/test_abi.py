@@ -83,7 +83,8 @@ def test_status_strings(lib):
                                  dict(G1=float("nan")), dict(G2=float("inf")), dict(rho0=0.0),
                                  dict(trace_every=-1), dict(prec=7), dict(psi_form=3),
                                  dict(rho_ref=float("nan")), dict(device=-1),
-                                 dict(nx=20000, ny=20000)])
+                                 dict(nx=20000, ny=20000), dict(nx=15456, ny=15456),
+                                 dict(nx=33, ny=4_000_000)])
 def test_invalid_parameters_rejected_on_host(lib, bad):
     kw = dict(nx=16, ny=16)
     kw.update(bad)

@@ -197,6 +197,38 @@ def test_fp32_full_size_8192_sampled():
     assert abs(e[3] - rho0.sum()) <= 1e-6 * rho0.sum()
 
 
+def test_fp32_largest_square_lattice_sampled():
+    """15424^2, the largest square lattice whose tiled populations (288 ceil(nx/32) ny
+    elements) keep the 32-bit offsets of the step below 2^31 (15456^2 is rejected on the
+    host). Three steps; sites near the last rows, the last tile column and the periodic
+    edges against oracle patches, as in the 8192^2 test; mass exact to 1e-6."""
+    torch = pytest.importorskip("torch")
+    n, steps, R = 15424, 3, 9
+    assert 288 * (n // 32) * n < 2 ** 31 <= 288 * ((n + 32) // 32) * (n + 32)
+    rho0 = inputs.noisy_density(n, n, seed=8, mean=0.7, amp=0.01, mode="rel")
+    rng = np.random.default_rng(6)
+    ys = np.array(list(rng.integers(0, n, 12)) + [0, n - 1, n - 1, n - 2, 7711])
+    xs = np.array(list(rng.integers(0, n, 12)) + [n - 1, 0, n - 1, n - 33, 7712])
+    with Lattice(torch.from_numpy(rho0).cuda(), G1=-5.0, G2=0.6, trace_every=10) as lat:
+        lat.step(steps)
+        f = torch.empty((3, n, n), dtype=torch.float64, device="cuda")
+        lat.fields(f[0], f[1], f[2])
+        e = lat.energy()
+        iy, ix = torch.from_numpy(ys).cuda(), torch.from_numpy(xs).cuda()
+        got = f[:, iy, ix].cpu().numpy()
+        umax = float(f[1:].abs().max())
+        del f
+    worst = [0.0, 0.0]
+    for k, (y, x) in enumerate(zip(ys, xs)):
+        patch = rho0[np.ix_(np.arange(y - R, y + R + 1) % n, np.arange(x - R, x + R + 1) % n)]
+        r, ux, uy, _ = oracle.run(patch, steps, G1=-5.0, G2=0.6)
+        worst[0] = max(worst[0], abs(got[0, k] - r[R, R]))
+        worst[1] = max(worst[1], abs(got[1, k] - ux[R, R]), abs(got[2, k] - uy[R, R]))
+    assert worst[0] <= 1e-5 * 0.71
+    assert worst[1] <= 1e-5 * max(umax, 1e-12)
+    assert abs(e[3] - rho0.sum()) <= 1e-6 * rho0.sum()
+
+
 # ----------------------------------------------------------------- edge cases
 def test_invalid_density_rejected():
     for bad in (np.nan, 0.0, -0.1, np.inf):
