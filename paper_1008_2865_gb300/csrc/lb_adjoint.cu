@@ -120,6 +120,58 @@ __device__ void accumulate_grid(double v[4], const AdjArgs& A)
     }
 }
 
+// Grid sum of two per-thread FP64 values added into A.acc[0..1], with the FP64
+// work of a block done by one warp (FP64 issues slowly on this part): the
+// threads' values meet in shared memory, warp 0 sums them in a fixed order,
+// and the last block to finish sums the block partials in block order.
+template <int NT>
+__device__ void accumulate_grid2(double v0, double v1, const AdjArgs& A)
+{
+    __shared__ double sh[2][NT];
+    __shared__ bool s_last;
+    const int tid = threadIdx.x;
+    sh[0][tid] = v0;
+    sh[1][tid] = v1;
+    __syncthreads();
+    double w0 = 0.0, w1 = 0.0;
+    if (tid < 32) {
+#pragma unroll
+        for (int j = tid; j < NT; j += 32) {
+            w0 += sh[0][j];
+            w1 += sh[1][j];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w0 += __shfl_down_sync(0xffffffffu, w0, o);
+            w1 += __shfl_down_sync(0xffffffffu, w1, o);
+        }
+        if (tid == 0) {
+            A.partials[2 * (size_t)blockIdx.x] = w0;
+            A.partials[2 * (size_t)blockIdx.x + 1] = w1;
+            __threadfence();
+            s_last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
+        }
+    }
+    __syncthreads();
+    if (!s_last || tid >= 32) return;
+    __threadfence();
+    w0 = w1 = 0.0;
+    for (unsigned int j = tid; j < gridDim.x; j += 32) {
+        w0 += __ldcg(A.partials + 2 * (size_t)j);
+        w1 += __ldcg(A.partials + 2 * (size_t)j + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        w0 += __shfl_down_sync(0xffffffffu, w0, o);
+        w1 += __shfl_down_sync(0xffffffffu, w1, o);
+    }
+    if (tid == 0) {
+        A.acc[0] += w0;
+        A.acc[1] += w1;
+        *A.counter = 0u;
+    }
+}
+
 __global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A)
 {
     const StepArgs<float>& a = A.a;
@@ -166,7 +218,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
     const int nx = a.nx, ny = a.ny, N = (int)a.N;
     const float om = a.omega;
     const float w[9] = {a.w0, a.w1, a.w1, a.w1, a.w1, a.w2, a.w2, a.w2, a.w2};
-    double v[4] = {0.0, 0.0, 0.0, 0.0};   // dJ/dG1, dJ/dG2
+    // dJ/dG1, dJ/dG2: FP32 per thread over up to 16 sites, then FP64
+    double g1 = 0.0, g2 = 0.0;
+    float f1 = 0.f, f2 = 0.f;
+    int nf = 0;
     for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
         const int y = s / nx, x = s % nx;
         float f[9];
@@ -214,10 +269,16 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
         A.dpsidrho[s] = dpr;
         A.Qx[s] = pc * Fbx;
         A.Qy[s] = pc * Fby;
-        v[0] += -(double)pc * (double)(Fbx * Swx + Fby * Swy);
-        v[1] += -(double)pc * (double)(Fbx * Spx + Fby * Spy);
+        f1 = fmaf(-pc, Fbx * Swx + Fby * Swy, f1);
+        f2 = fmaf(-pc, Fbx * Spx + Fby * Spy, f2);
+        if (++nf == 16) {
+            g1 += f1;
+            g2 += f2;
+            f1 = f2 = 0.f;
+            nf = 0;
+        }
     }
-    accumulate_grid<kAdjThreads>(v, A);
+    accumulate_grid2<kAdjThreads>(g1 + f1, g2 + f2, A);
 }
 
 __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_b(const AdjArgs A)

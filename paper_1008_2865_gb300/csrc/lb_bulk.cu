@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
         if (REDUCE && out_site) {
             energy_site(rows, pc, a, es, em, eb);
             ms += d;
-            if (((r - y0) & 15) == 15) {
+            if (((r - y0) & 63) == 63) {
                 d_es += es; d_em += em; d_eb += eb; d_ms += ms;
                 es = em = eb = ms = 0.f;
             }

@@ -141,26 +141,27 @@ __device__ __forceinline__ float dpsi_of(float d, const StepArgs<T>& a)
 }
 
 // Deterministic sum of 4 doubles over a CTA of NT threads (NT a multiple of
-// 32, at most 1024); the result is valid in thread 0.
+// 32, at most 1024); the result is valid in thread 0. The threads' values meet
+// in shared memory and warp 0 alone does the FP64 adds (fixed strided order,
+// then a fixed shuffle tree): FP64 issues slowly on this part, so the adds of
+// one warp instead of every warp's shuffle tree.
 template <int NT>
 __device__ void block_sum4(double v[4])
 {
-    __shared__ double red[NT / 32][4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double red[4][NT];
+    const int tid = threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) red[warp][k] = v[k];
-    }
+    for (int k = 0; k < 4; ++k) red[k][tid] = v[k];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < NT / 32; ++w) {
+    if (tid < 32) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] += red[w][k];
+        for (int k = 0; k < 4; ++k) {
+            double w = red[k][tid];
+#pragma unroll
+            for (int j = tid + 32; j < NT; j += 32) w += red[k][j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+            v[k] = w;
         }
     }
     __syncthreads();

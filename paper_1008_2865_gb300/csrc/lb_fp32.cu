@@ -29,7 +29,7 @@
 //      rows r-1, r, r+1; row r-1 is then complete and its dpsi(t+1) is written.
 // One __syncthreads per row orders the exchange and the ring updates.
 // REDUCE launches also accumulate mass and the Sec. 5 pseudo-energies of
-// state t (FP32 per thread for 16 rows, then FP64), reduce them per CTA in
+// state t (FP32 per thread for 64 rows, then FP64), reduce them per CTA in
 // FP64 and let the last CTA to finish sum all CTA partials in a fixed order
 // into one trace row — deterministic for a given launch shape.
 #include "lb_device.cuh"
@@ -182,7 +182,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
             // Sec. 5 energies of state t at (x, r); the dpsi rows r-2..r+2 stay in the
             // ring until the next iteration overwrites slot (r+4) & 7
             energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
-            if (((r - y0) & 15) == 15) {
+            if (((r - y0) & 63) == 63) {
                 d_es += es; d_em += em; d_eb += eb; d_ms += ms;
                 es = em = eb = ms = 0.f;
             }
