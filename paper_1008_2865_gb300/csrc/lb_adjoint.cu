@@ -37,6 +37,7 @@ using namespace lbsc::dev;
 namespace {
 
 constexpr int kAdjThreads = 256;
+constexpr int kAdjMaxBlocks = 152 * (2048 / kAdjThreads);   // one full wave of threads
 
 // Periodic neighbourhood of site (x, y), computed once per site (nx, ny >= 5):
 // columns x-2 .. x+2 and row offsets (y-2 .. y+2) * nx.
@@ -324,7 +325,7 @@ __global__ void k_adj_grad_init(const float* __restrict__ lam, int N, float w0, 
 int adj_grid(long long n)
 {
     long long b = (n + kAdjThreads - 1) / kAdjThreads;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > kAdjMaxBlocks) b = kAdjMaxBlocks;
     return (int)(b < 1 ? 1 : b);
 }
 
@@ -394,7 +395,7 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
               cudaMalloc((void**)&scr, sizeof(float) * 6 * (size_t)N) == cudaSuccess &&
               cudaMalloc((void**)&tgt, sizeof(double) * N) == cudaSuccess &&
               cudaMalloc((void**)&acc, sizeof(double) * 8) == cudaSuccess &&
-              cudaMalloc((void**)&part, sizeof(double) * 4 * 152 * 8) == cudaSuccess &&
+              cudaMalloc((void**)&part, sizeof(double) * 4 * kAdjMaxBlocks) == cudaSuccess &&
               cudaMalloc((void**)&cnt, sizeof(unsigned int)) == cudaSuccess &&
               (grad_on_dev || cudaMalloc((void**)&grad_dev, sizeof(double) * N) == cudaSuccess);
     if (!ok) {
