@@ -373,8 +373,9 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
         cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->err, 0, sizeof(int), s->stream) != cudaSuccess)
         return bail(LB_ERR_CUDA);
-    if (p->prec != LB_FP64) {
+    if (p->prec != LB_FP64 && g_pitch(p->nx) != 9 * p->nx) {
         // the padding columns of the tiled populations hold zeros in both buffers
+        // (nx not a multiple of 32; otherwise every element is written by the init)
         const size_t gb = elem_size(p->prec) * (size_t)g_elems(p->nx, p->ny);
         if (cudaMemsetAsync(s->g[0], 0, gb, s->stream) != cudaSuccess ||
             cudaMemsetAsync(s->g[1], 0, gb, s->stream) != cudaSuccess)
