@@ -11,10 +11,12 @@
 // Work decomposition. A CTA of BX threads owns a strip of BX-2 output
 // columns and `rows` output rows; thread k sits on column x0-1+k, so the two
 // edge threads are the one-column halo whose collisions the interior needs.
-// The CTA marches down its rows. For collision row r it
+// The CTA marches over its rows, down for even row chunks and up for odd ones
+// (so that the two CTAs reading a chunk boundary's halo row read it at about
+// the same time, and the second read hits L2). For collision row r it
 //   1. reads the 9 populations f_i(x, r) of its own site (one base address,
-//      immediate offsets) — the loads of row r+1 are issued before row r is
-//      computed;
+//      immediate offsets) — the loads of the next row are issued before row r
+//      is computed;
 //   2. forms rho, j (Eqs. 2-3) and reads psi(t) of the 25-site stencil from a
 //      ring of 8 dpsi rows kept in shared memory (each dpsi row is read from
 //      HBM once per CTA);
@@ -25,8 +27,8 @@
 //      right-moving and three left-moving values go to the neighbouring
 //      threads through shared memory, and every thread stores f(t+1) of its
 //      own column — the speeds with c_y = -1, 0, +1 into rows r-1, r, r+1.
-//      The same values summed in three rolling registers give rho(t+1) of
-//      rows r-1, r, r+1; row r-1 is then complete and its dpsi(t+1) is written.
+//      The same values, summed per speed group in a fixed order, give
+//      rho(t+1); the row behind r is then complete and its dpsi(t+1) is written.
 // One __syncthreads per row orders the exchange and the ring updates.
 // REDUCE launches also accumulate mass and the Sec. 5 pseudo-energies of
 // state t (FP32 per thread for 64 rows, then FP64), reduce them per CTA in
@@ -41,13 +43,6 @@ namespace {
 
 using namespace dev;
 
-// Advance a row offset (row * nx) by one row with periodic wrap.
-__device__ __forceinline__ int next_row(int off, int nx, int N)
-{
-    off += nx;
-    return off == N ? 0 : off;
-}
-
 // Resident warps per SM the register budget is cut for: 40 warps (48 registers)
 // for the plain steps and 32 warps (64 registers) for the reduction step, the
 // most that compile without spills (48 warps at 40 registers spill, and run
@@ -57,17 +52,30 @@ struct StepWarps {
     static constexpr int value = REDUCE ? 32 : 40;
 };
 
-// One CTA's tile of the step: output columns [bx (BX-2), +BX-2) and output
-// rows [by rows, +rows). With REDUCE, v receives this thread's FP64 partial
-// sums {E_s, E_m, E_bulk, sum of rho - rho_ref} of state t over its sites.
-template <typename T, int BX, bool REDUCE, bool OM1>
-__device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, double v[4])
+// Advance a row offset (row * stride, periodic over `total`) by one row in
+// direction DIR (+1 down, -1 up).
+template <int DIR>
+__device__ __forceinline__ int step_row(int off, int stride, int total)
 {
-    constexpr int W = BX + 4;
-    __shared__ float win[8][W];              // dpsi(t) rows, slot = row & 7
-    __shared__ float4 exR[2][BX + 2];        // right-moving f*: speeds 8, 1, 5 (cy = -1, 0, +1)
-    __shared__ float4 exL[2][BX + 2];        // left-moving f*: speeds 7, 3, 6
+    if (DIR > 0) {
+        off += stride;
+        return off == total ? 0 : off;
+    }
+    return (off == 0 ? total : off) - stride;
+}
 
+// One CTA's tile of the step: output columns [bx (BX-2), +BX-2) and output
+// rows [y0, y1) = [by rows, +rows), marched in direction DIR: down from row
+// y0-1 (DIR = +1) or up from row y1 (DIR = -1). When neighbouring row chunks
+// march in opposite directions, the two CTAs that read a chunk boundary's halo
+// row reach it at about the same time and the second read hits L2. With
+// REDUCE, v receives this thread's FP64 partial sums {E_s, E_m, E_bulk, sum of
+// rho - rho_ref} of state t over its sites.
+template <typename T, int BX, bool REDUCE, bool OM1, int DIR>
+__device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int by, double v[4],
+                                              float (*win)[BX + 4], float4 (*exR)[BX + 2],
+                                              float4 (*exL)[BX + 2])
+{
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
     const int N = (int)a.N;
@@ -75,50 +83,57 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
     const int x0 = bx * (BX - 2);
     const int y0 = by * a.rows;
     const int y1 = min(y0 + a.rows, ny);
+    const int nrows = y1 - y0;
     const int txe = min(BX - 2, nx - x0);
     const bool out_col = tid >= 1 && tid <= txe;
     const int xc = wrapi(x0 - 1 + tid, nx);
     const int pc0 = wrapi(x0 - 3 + tid, nx);
     const int pc1 = wrapi(x0 - 3 + BX + (tid & 3), nx);
     const int cx = tcol(xc);
+    const int r0 = DIR > 0 ? y0 - 1 : y1;    // first collision row
 
-    for (int rr = y0 - 3; rr <= y0 + 1; ++rr) {
+    for (int rr = r0 - 2; rr <= r0 + 2; ++rr) {
         const float* src = a.dpsi_in + wrapi(rr, ny) * nx;
         win[rr & 7][tid] = __ldg(src + pc0);
         if (tid < 4) win[rr & 7][BX + tid] = __ldg(src + pc1);
     }
     // Row offsets (row * P) of g, periodic, kept incrementally: at the top of
-    // iteration r, s0, s1, s2 hold rows r-1, r, r+1 and oq the dpsi row r+3.
-    int s0 = wrapi(y0 - 2, ny) * P;
-    int s1 = wrapi(y0 - 1, ny) * P;
-    int s2 = wrapi(y0, ny) * P;
-    int oq = wrapi(y0 + 2, ny) * nx;
+    // iteration r, sb, sc, sa hold rows r-DIR (behind), r, r+DIR (ahead) and oq
+    // the dpsi row r+3 DIR.
+    int sb = wrapi(r0 - DIR, ny) * P;
+    int sc = wrapi(r0, ny) * P;
+    int sa = wrapi(r0 + DIR, ny) * P;
+    int oq = wrapi(r0 + 3 * DIR, ny) * nx;
 
     float f[9];
-    load_site(f, a.g_in + (s1 + cx));                  // collision row y0 - 1
+    load_site(f, a.g_in + (sc + cx));
     __syncthreads();
 
-    float acc_m = 0.f, acc_0 = 0.f;
+    // rho(t+1) of a row from its three speed groups (c_y = +1, 0, -1), summed as
+    // (G+ + G0) + G- whatever the direction: hb = ahead-group sum of the behind
+    // row, zb = zero-group sum of the behind row, hc = ahead-group sum of row r.
+    float hb = 0.f, zb = 0.f, hc = 0.f;
     float es = 0.f, em = 0.f, eb = 0.f, ms = 0.f;
     double d_es = 0.0, d_em = 0.0, d_eb = 0.0, d_ms = 0.0;
 
-    for (int r = y0 - 1; r <= y1; ++r) {
-        // ---- prefetch: dpsi row r+3 and the populations of row r+1
-        const bool need_psi = r <= y1 - 1;
+    for (int k = 0; k <= nrows + 1; ++k) {
+        const int r = r0 + DIR * k;
+        // ---- prefetch: dpsi row r+3 DIR and the populations of row r+DIR
+        const bool more = k <= nrows;
         float pn0 = 0.f, pn1 = 0.f;
-        if (need_psi) {
+        if (more) {
             const float* src = a.dpsi_in + oq;
             pn0 = __ldg(src + pc0);
             if (tid < 4) pn1 = __ldg(src + pc1);
         }
-        oq = next_row(oq, nx, N);
+        oq = step_row<DIR>(oq, nx, N);
         float fn[9];
-        if (r < y1) load_site(fn, a.g_in + (s2 + cx));
+        if (more) load_site(fn, a.g_in + (sa + cx));
 
         // ---- force from the dpsi(t) ring, then moments and collision
         const float* rows[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) rows[k] = &win[(r - 2 + k) & 7][tid + 2];
+        for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
         const float pc = a.psi_ref + rows[2][0];
         float Sx, Sy;
         force_sums(rows, a, Sx, Sy);
@@ -131,58 +146,64 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
         // ---- exchange post-collision values with the neighbouring columns
         exR[r & 1][tid + 1] = make_float4(gs[8], gs[1], gs[5], 0.f);
         exL[r & 1][tid + 1] = make_float4(gs[7], gs[3], gs[6], 0.f);
-        if (need_psi) {
-            win[(r + 3) & 7][tid] = pn0;
-            if (tid < 4) win[(r + 3) & 7][BX + tid] = pn1;
+        if (more) {
+            win[(r + 3 * DIR) & 7][tid] = pn0;
+            if (tid < 4) win[(r + 3 * DIR) & 7][BX + tid] = pn1;
         }
         // ---- f(t+1) = f*(x - c_i) (Eq. 1) for the own column: the speeds with
-        // c_y = -1, 0, +1 land in rows r-1, r, r+1. The own-column speeds 4, 0, 2
-        // are stored now, the six from the neighbouring columns after the barrier.
-        const bool st_m = out_col && r - 1 >= y0;
+        // c_y = -DIR land in the behind row, c_y = 0 in row r, c_y = +DIR in the
+        // ahead row. The own-column speeds are stored now, the six from the
+        // neighbouring columns after the barrier.
+        const int rb = r - DIR, ra = r + DIR;
+        const bool st_b = out_col && rb >= y0 && rb < y1;
         const bool st_0 = out_site;
-        const bool st_p = out_col && r + 1 < y1;
-        if (st_m) st_(a.g_out + (s0 + cx) + kTileW * 4, gs[4]);
-        if (st_0) st_(a.g_out + (s1 + cx), gs[0]);
-        if (st_p) st_(a.g_out + (s2 + cx) + kTileW * 2, gs[2]);
-        acc_m += gs[4];
-        acc_0 += gs[0];
-        float acc_p = gs[2];
+        const bool st_a = out_col && ra >= y0 && ra < y1;
+        constexpr int ib = DIR > 0 ? 4 : 2, ia = DIR > 0 ? 2 : 4;   // own speeds with c_y = -DIR, +DIR
+        if (st_b) st_(a.g_out + (sb + cx) + kTileW * ib, gs[ib]);
+        if (st_0) st_(a.g_out + (sc + cx), gs[0]);
+        if (st_a) st_(a.g_out + (sa + cx) + kTileW * ia, gs[ia]);
+        const float own_b = gs[ib], own_0 = gs[0], own_a = gs[ia];
         __syncthreads();
-        const float4 R = exR[r & 1][tid];       // from column x-1
-        const float4 L = exL[r & 1][tid + 2];   // from column x+1
-        if (st_m) {
-            T* o = a.g_out + (s0 + cx);
-            st_(o + kTileW * 7, L.x);
-            st_(o + kTileW * 8, R.x);
+        const float4 R = exR[r & 1][tid];       // from column x-1: speeds 8, 1, 5
+        const float4 L = exL[r & 1][tid + 2];   // from column x+1: speeds 7, 3, 6
+        const float Rb = DIR > 0 ? R.x : R.z, Lb = DIR > 0 ? L.x : L.z;
+        const float Ra = DIR > 0 ? R.z : R.x, La = DIR > 0 ? L.z : L.x;
+        if (st_b) {
+            T* o = a.g_out + (sb + cx);
+            st_(o + kTileW * (DIR > 0 ? 7 : 6), Lb);
+            st_(o + kTileW * (DIR > 0 ? 8 : 5), Rb);
         }
         if (st_0) {
-            T* o = a.g_out + (s1 + cx);
+            T* o = a.g_out + (sc + cx);
             st_(o + kTileW * 1, R.y);
             st_(o + kTileW * 3, L.y);
         }
-        if (st_p) {
-            T* o = a.g_out + (s2 + cx);
-            st_(o + kTileW * 5, R.z);
-            st_(o + kTileW * 6, L.z);
+        if (st_a) {
+            T* o = a.g_out + (sa + cx);
+            st_(o + kTileW * (DIR > 0 ? 6 : 7), La);
+            st_(o + kTileW * (DIR > 0 ? 5 : 8), Ra);
         }
-        acc_m += R.x + L.x;
-        acc_0 += R.y + L.y;
-        acc_p += R.z + L.z;
-        // rho(t+1) of row r-1 is complete
-        if (st_m) a.dpsi_out[(r - 1) * nx + xc] = dpsi_of(acc_m, a);
-        acc_m = acc_0;
-        acc_0 = acc_p;
-        s0 = s1;
-        s1 = s2;
-        s2 += P;
-        if (s2 == NP) s2 = 0;
+        const float gb = own_b + (Rb + Lb);     // behind-group sum into row r-DIR
+        const float g0 = own_0 + (R.y + L.y);   // zero-group sum of row r
+        const float ga = own_a + (Ra + La);     // ahead-group sum into row r+DIR
+        // rho(t+1) of the behind row is complete: (G+ + G0) + G-
+        if (st_b) {
+            const float rho1 = DIR > 0 ? (hb + zb) + gb : (gb + zb) + hb;
+            a.dpsi_out[rb * nx + xc] = dpsi_of(rho1, a);
+        }
+        hb = hc;
+        zb = g0;
+        hc = ga;
+        sb = sc;
+        sc = sa;
+        sa = step_row<DIR>(sa, P, NP);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fn[i];
         if (REDUCE && out_site) {
             // Sec. 5 energies of state t at (x, r); the dpsi rows r-2..r+2 stay in the
-            // ring until the next iteration overwrites slot (r+4) & 7
+            // ring until the next iteration overwrites slot (r + 4 DIR) & 7
             energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
-            if (((r - y0) & 63) == 63) {
+            if ((k & 63) == 63) {
                 d_es += es; d_em += em; d_eb += eb; d_ms += ms;
                 es = em = eb = ms = 0.f;
             }
@@ -197,12 +218,30 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
     }
 }
 
+// The tile of chunk `by`. With ALTERNATE, plain steps march down in even
+// chunks and up in odd ones; reduction steps, and every tile of a batch, march
+// down. Fields do not depend on the direction (each site's arithmetic, and the
+// order of the rho(t+1) sum, are the same either way); the per-thread energy
+// and mass sums do, so keeping the reduction steps on one direction keeps a
+// batch replica's trace bit-identical to the same lattice run alone.
+template <typename T, int BX, bool REDUCE, bool OM1, bool ALTERNATE>
+__device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, double v[4])
+{
+    __shared__ float win[8][BX + 4];          // dpsi(t) rows, slot = row & 7
+    __shared__ float4 exR[2][BX + 2];        // right-moving f*: speeds 8, 1, 5 (cy = -1, 0, +1)
+    __shared__ float4 exL[2][BX + 2];        // left-moving f*: speeds 7, 3, 6
+    if (ALTERNATE && !REDUCE && (by & 1))
+        step_tile_dir<T, BX, REDUCE, OM1, -1>(a, bx, by, v, win, exR, exL);
+    else
+        step_tile_dir<T, BX, REDUCE, OM1, +1>(a, bx, by, v, win, exR, exL);
+}
+
 template <typename T, int BX, bool REDUCE, bool OM1>
 __global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / BX)
     k_step(const StepArgs<T> a)
 {
     double v[4];
-    step_tile<T, BX, REDUCE, OM1>(a, blockIdx.x, blockIdx.y, v);
+    step_tile<T, BX, REDUCE, OM1, true>(a, blockIdx.x, blockIdx.y, v);
     if (REDUCE) {
         const unsigned int nb = gridDim.x * gridDim.y;
         if (last_block_total<BX>(v, a.partials, a.counter, nb)) {
@@ -234,7 +273,7 @@ __global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
         if (threadIdx.x == 0) sa = args[tl.x];
         __syncthreads();
         double v[4];
-        step_tile<T, BX, REDUCE, OM1>(sa, tl.y, tl.z, v);
+        step_tile<T, BX, REDUCE, OM1, false>(sa, tl.y, tl.z, v);
         if (REDUCE) {
             block_sum4<BX>(v);
             if (threadIdx.x == 0) {

@@ -19,7 +19,7 @@ import threading
 
 BLOCK_X = (64, 96, 128, 192, 256)
 BULK_BLOCK_X = (64, 128, 256)
-ROWS = (4, 8, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384)
+ROWS = (4, 8, 16, 24, 32, 48, 56, 64, 72, 80, 96, 128, 192, 256, 384)
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_launch.json")
 _lock = threading.Lock()
 
