@@ -108,7 +108,8 @@ lb_status validate(const lb_params* p)
 // the bulk-copy rings on GB300 for the 8192^2 lattice; the tuner may still pick
 // the rings) with 128-thread strips, or 64-thread strips for lattices whose
 // state fits in L2 (512^2: 11.1 us per step against 12.5 us); rows chosen for
-// about four waves of 40 resident warps per SM on a 152-SM part, at least 8
+// about five waves of 40 resident warps per SM on a 152-SM part (8192^2: 72
+// rows, 4.95 waves, the tuned shape), at least 8
 // (small lattices have few columns, so short chunks are what gives them enough
 // CTAs: 512^2 steps in 11.1 us with 8-row chunks against 15.2 us with 16).
 Fp32Launch default_launch(int nx, int ny, lb_precision prec)
@@ -117,7 +118,7 @@ Fp32Launch default_launch(int nx, int ny, lb_precision prec)
     Fp32Launch L{128, 64, 0};
     if ((long long)nx * ny * 80 <= (128LL << 20)) L.block_x = 64;
     const long long strips = (nx + L.block_x - 3) / (L.block_x - 2);
-    const long long target = 152LL * (40 * 32 / L.block_x) * 4;
+    const long long target = 152LL * (40 * 32 / L.block_x) * 5;
     long long rows = (strips * ny + target - 1) / target;
     if (rows < 8) rows = 8;
     if (rows > 512) rows = 512;
