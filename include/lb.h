@@ -109,7 +109,9 @@ lb_status lb_energy(lb_state* s, double out[4]);
 
 /* Density rho = sum f_i and velocity u = sum c_i f_i / rho (Eqs. 2-3) of the
  * current state, written as N doubles each into caller-owned host or device
- * arrays; any of the three may be NULL. Synchronises the stream.
+ * arrays; any of the three may be NULL. Device and pinned host arrays are
+ * written directly by one kernel pass; pageable host arrays go through a device
+ * buffer of N doubles that the state keeps. Synchronises the stream.
  * Errors: LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA. */
 lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy);
 

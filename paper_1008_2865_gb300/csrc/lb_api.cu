@@ -71,20 +71,23 @@ Couplings couplings(double G1, double G2)
 
 }  // namespace lbsc
 
-
-
-
 namespace {
 
-bool is_device_ptr(const void* p)
+// Where a kernel can read or write an array directly: device (or managed) memory
+// as it is, pinned host memory through its device alias (read or written over
+// the host link by the kernel, no staging copy); nullptr for pageable host memory.
+double* device_view(double* p)
 {
-    if (!p) return false;
+    if (!p) return nullptr;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return nullptr;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return p;
+    if (at.type == cudaMemoryTypeHost && at.devicePointer)
+        return static_cast<double*>(at.devicePointer);
+    return nullptr;
 }
 
 lb_status validate(const lb_params* p)
@@ -354,23 +357,26 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
         free_state(s);
         return LB_ERR_OOM;
     }
-    // rho_init on the device (copied when it is host memory)
+    // rho_init where the kernels can read it: in place (device memory, or pinned
+    // host memory read over the host link), else copied into a temporary
     double* rho_dev = nullptr;   // a temporary, not one of the state's guarded buffers
-    const bool dev_src = is_device_ptr(rho_init);
-    if (cudaMalloc((void**)&rho_dev, sizeof(double) * N) != cudaSuccess) {
-        cudaGetLastError();
-        free_state(s);
-        return LB_ERR_OOM;
+    const double* rho_in = device_view(const_cast<double*>(rho_init));
+    if (!rho_in) {
+        if (cudaMalloc((void**)&rho_dev, sizeof(double) * N) != cudaSuccess) {
+            cudaGetLastError();
+            free_state(s);
+            return LB_ERR_OOM;
+        }
+        rho_in = rho_dev;
     }
     auto bail = [&](lb_status st) {
-        cudaFree(rho_dev);
+        if (rho_dev) cudaFree(rho_dev);
         cudaGetLastError();
         free_state(s);
         return st;
     };
-    if (cudaMemcpyAsync(rho_dev, rho_init, sizeof(double) * N,
-                        dev_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                        s->stream) != cudaSuccess ||
+    if ((rho_dev && cudaMemcpyAsync(rho_dev, rho_init, sizeof(double) * N, cudaMemcpyHostToDevice,
+                                    s->stream) != cudaSuccess) ||
         cudaMemsetAsync(s->counter, 0, sizeof(unsigned int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->trace_count, 0, sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream) != cudaSuccess ||
@@ -384,7 +390,7 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
             cudaMemsetAsync(s->g[1], 0, gb, s->stream) != cudaSuccess)
             return bail(LB_ERR_CUDA);
     }
-    if (rho_check_sum(rho_dev, N, s->partials, s->counter, s->res, s->flag, s->stream) !=
+    if (rho_check_sum(rho_in, N, s->partials, s->counter, s->res, s->flag, s->stream) !=
         cudaSuccess)
         return bail(LB_ERR_CUDA);
     double sum = 0.0;
@@ -402,16 +408,16 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
     s->rho_ref = (double)(float)(p->rho_ref > 0.0 ? p->rho_ref : sum / (double)N);
     cudaError_t e;
     if (p->prec == LB_FP64)
-        e = fp64_init(s->f64[0], rho_dev, p->nx, p->ny, s->stream);
+        e = fp64_init(s->f64[0], rho_in, p->nx, p->ny, s->stream);
     else if (p->prec == LB_FP32)
-        e = delta_init<float>(static_cast<float*>(s->g[0]), s->dpsi[0], rho_dev, p->nx, p->ny,
+        e = delta_init<float>(static_cast<float*>(s->g[0]), s->dpsi[0], rho_in, p->nx, p->ny,
                               s->rho_ref, p->rho0, s->stream);
     else
-        e = delta_init<__half>(static_cast<__half*>(s->g[0]), s->dpsi[0], rho_dev, p->nx, p->ny,
+        e = delta_init<__half>(static_cast<__half*>(s->g[0]), s->dpsi[0], rho_in, p->nx, p->ny,
                                s->rho_ref, p->rho0, s->stream);
     if (e != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess)
         return bail(LB_ERR_CUDA);
-    cudaFree(rho_dev);
+    if (rho_dev) cudaFree(rho_dev);
     *out = s;
     return LB_OK;
 }
@@ -459,6 +465,16 @@ lb_status lb_energy(lb_state* s, double out[4])
     return LB_OK;
 }
 
+static cudaError_t fields_into(lb_state* s, double* r, double* x, double* y)
+{
+    if (s->p.prec == LB_FP64) return fp64_fields(s->f64[s->cur], s->p.nx, s->p.ny, r, x, y, s->stream);
+    if (s->p.prec == LB_FP32)
+        return delta_fields<float>(static_cast<const float*>(s->g[s->cur]), s->p.nx, s->p.ny,
+                                   s->rho_ref, r, x, y, s->stream);
+    return delta_fields<__half>(static_cast<const __half*>(s->g[s->cur]), s->p.nx, s->p.ny,
+                                s->rho_ref, r, x, y, s->stream);
+}
+
 lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy)
 {
     NvtxRange nvtx_range("lb_fields");
@@ -467,37 +483,29 @@ lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy)
     LB_CUDA(s, cudaSetDevice(s->p.device));
     const long long N = s->N;
     double* outs[3] = {rho, ux, uy};
+    double* views[3];
+    for (int k = 0; k < 3; ++k) views[k] = device_view(outs[k]);
+    // every output a kernel can write directly: one pass over the populations
+    if (views[0] || views[1] || views[2]) {
+        if (fields_into(s, views[0], views[1], views[2]) != cudaSuccess) return fail_cuda(s);
+    }
+    // pageable host outputs: through a device buffer, one field at a time
     for (int k = 0; k < 3; ++k) {
-        if (!outs[k]) continue;
-        const bool dev = is_device_ptr(outs[k]);
-        double* dst = outs[k];
-        if (!dev) {
+        if (!outs[k] || views[k]) continue;
+        if (!s->field_tmp) {
+            s->field_tmp = static_cast<double*>(state_alloc(s, sizeof(double) * N));
             if (!s->field_tmp) {
-                s->field_tmp = static_cast<double*>(state_alloc(s, sizeof(double) * N));
-                if (!s->field_tmp) {
-                    cudaGetLastError();
-                    s->field_tmp = nullptr;
-                    return LB_ERR_OOM;
-                }
+                cudaGetLastError();
+                s->field_tmp = nullptr;
+                return LB_ERR_OOM;
             }
-            dst = s->field_tmp;
         }
-        double* r = k == 0 ? dst : nullptr;
-        double* x = k == 1 ? dst : nullptr;
-        double* y = k == 2 ? dst : nullptr;
-        cudaError_t e;
-        if (s->p.prec == LB_FP64)
-            e = fp64_fields(s->f64[s->cur], s->p.nx, s->p.ny, r, x, y, s->stream);
-        else if (s->p.prec == LB_FP32)
-            e = delta_fields<float>(static_cast<const float*>(s->g[s->cur]), s->p.nx, s->p.ny,
-                                    s->rho_ref, r, x, y, s->stream);
-        else
-            e = delta_fields<__half>(static_cast<const __half*>(s->g[s->cur]), s->p.nx, s->p.ny,
-                                     s->rho_ref, r, x, y, s->stream);
-        if (e != cudaSuccess) return fail_cuda(s);
-        if (!dev)
-            LB_CUDA(s, cudaMemcpyAsync(outs[k], dst, sizeof(double) * N, cudaMemcpyDeviceToHost,
-                                       s->stream));
+        double* t = s->field_tmp;
+        if (fields_into(s, k == 0 ? t : nullptr, k == 1 ? t : nullptr, k == 2 ? t : nullptr) !=
+            cudaSuccess)
+            return fail_cuda(s);
+        LB_CUDA(s, cudaMemcpyAsync(outs[k], t, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                                   s->stream));
     }
     LB_CUDA(s, cudaStreamSynchronize(s->stream));
     return check_err(s);

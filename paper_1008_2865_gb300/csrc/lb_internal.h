@@ -174,7 +174,7 @@ struct lb_state {
     int* trace_count = nullptr;
     double* res = nullptr;         // 4 doubles of results
     int* flag = nullptr;
-    double* field_tmp = nullptr;   // N doubles, allocated on the first host-destined lb_fields
+    double* field_tmp = nullptr;   // N doubles, allocated on the first lb_fields into pageable host memory
     // every device buffer of the state, with a guard region on each side
     struct Alloc {
         void* base;

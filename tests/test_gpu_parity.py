@@ -273,6 +273,32 @@ def test_device_pointers_and_partial_fields():
         assert np.array_equal(only_ux, h_ux)
 
 
+def test_pinned_host_buffers_match_pageable_and_device():
+    """Pinned host memory is read (init) and written (fields) in place by the kernels;
+    the results equal those through pageable host memory and device memory."""
+    torch = pytest.importorskip("torch")
+    rho0 = inputs.noisy_density(301, 77, seed=4, mean=0.7, amp=0.01, mode="rel")
+    pinned_in = torch.from_numpy(rho0).pin_memory()
+    res = []
+    for src in (rho0, pinned_in, torch.from_numpy(rho0).cuda()):
+        with Lattice(src, G1=-5.0, G2=0.6) as lat:
+            lat.step(25)
+            pageable = lat.fields()
+            pinned = [torch.empty((77, 301), dtype=torch.float64).pin_memory() for _ in range(3)]
+            lat.fields(*pinned)
+            only_uy = torch.empty((77, 301), dtype=torch.float64).pin_memory()
+            lat.fields(uy=only_uy)
+            dev = [torch.empty((77, 301), dtype=torch.float64, device="cuda") for _ in range(3)]
+            lat.fields(dev[0], dev[1], dev[2])
+        for a, b, c in zip(pageable, pinned, dev):
+            assert np.array_equal(a, b.numpy()) and np.array_equal(a, c.cpu().numpy())
+        assert np.array_equal(pageable[2], only_uy.numpy())
+        res.append(pageable)
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            assert np.array_equal(a, b)
+
+
 def test_guard_check_sees_a_write_outside_a_buffer():
     """The guard check is not vacuous: a byte changed just past a buffer (by a host-side
     cudaMemset through the test hook, never by a kernel) is reported, buffer by buffer."""
