@@ -44,8 +44,9 @@ def test_batch_matches_single_runs_bit_for_bit(use_graph, launch):
         assert got[i][2] == en
 
 
-@pytest.mark.parametrize("launch", [(128, 72), (128, 16), (64, 8)])
-def test_march_direction_does_not_change_the_fields(launch):
+@pytest.mark.parametrize("launch,prec", [((128, 72), "fp32"), ((128, 16), "fp32"), ((64, 8), "fp32"),
+                                         ((128, 72), "fp16_delta")])
+def test_march_direction_does_not_change_the_fields(launch, prec):
     """On a lattice whose state exceeds L2 (1536^2 x 80 B = 189 MB) the plain steps of a
     single lattice march down in even row chunks and up in odd ones, while a batch
     always marches down: the fields are the same bit for bit (the rho(t+1) sum has a
@@ -53,12 +54,12 @@ def test_march_direction_does_not_change_the_fields(launch):
     n = 1536
     rho0 = inputs.noisy_density(n, n, seed=77, mean=0.7, amp=0.01, mode="rel")
     steps = 23
-    with Lattice(rho0, G1=-5.0, G2=0.6, trace_every=10) as lat:
+    with Lattice(rho0, G1=-5.0, G2=0.6, trace_every=10, prec=prec) as lat:
         lat.set_launch(launch[0], launch[1], 0)
         lat.step(steps)
         f1 = lat.fields()
         t1 = lat.trace()
-    with Batch([rho0], G1=-5.0, G2=[0.6], trace_every=10) as b:
+    with Batch([rho0], G1=-5.0, G2=[0.6], trace_every=10, prec=prec) as b:
         b.set_launch(launch[0], launch[1], 1)
         b.step(steps)
         f2 = b.fields(0)
