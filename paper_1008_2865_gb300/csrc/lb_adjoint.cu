@@ -121,42 +121,42 @@ __device__ void accumulate_grid(double v[4], const AdjArgs& A)
     }
 }
 
-// Grid sum of two per-thread FP64 values added into A.acc[0..1], with the FP64
-// work of a block done by one warp (FP64 issues slowly on this part): the
-// threads' values meet in shared memory, warp 0 sums them in a fixed order,
-// and the last block to finish sums the block partials in block order.
+// Grid sum of two per-thread values added into A.acc[0..1] with as little FP64
+// work as possible (FP64 issues slowly on this part): a fixed FP32 shuffle tree
+// in each warp, the warp sums converted to FP64 and added by warp 0 in a fixed
+// order, and the last block to finish sums the block partials in block order.
 template <int NT>
-__device__ void accumulate_grid2(double v0, double v1, const AdjArgs& A)
+__device__ void accumulate_grid2(float v0, float v1, const AdjArgs& A)
 {
-    __shared__ double sh[2][NT];
+    constexpr int NW = NT / 32;
+    __shared__ float sh[2][NW];
     __shared__ bool s_last;
-    const int tid = threadIdx.x;
-    sh[0][tid] = v0;
-    sh[1][tid] = v1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_down_sync(0xffffffffu, v0, o);
+        v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    }
+    if (lane == 0) {
+        sh[0][warp] = v0;
+        sh[1][warp] = v1;
+    }
     __syncthreads();
-    double w0 = 0.0, w1 = 0.0;
-    if (tid < 32) {
-#pragma unroll
-        for (int j = tid; j < NT; j += 32) {
-            w0 += sh[0][j];
-            w1 += sh[1][j];
+    if (tid == 0) {
+        double w0 = 0.0, w1 = 0.0;
+        for (int k = 0; k < NW; ++k) {
+            w0 += (double)sh[0][k];
+            w1 += (double)sh[1][k];
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            w0 += __shfl_down_sync(0xffffffffu, w0, o);
-            w1 += __shfl_down_sync(0xffffffffu, w1, o);
-        }
-        if (tid == 0) {
-            A.partials[2 * (size_t)blockIdx.x] = w0;
-            A.partials[2 * (size_t)blockIdx.x + 1] = w1;
-            __threadfence();
-            s_last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
-        }
+        A.partials[2 * (size_t)blockIdx.x] = w0;
+        A.partials[2 * (size_t)blockIdx.x + 1] = w1;
+        __threadfence();
+        s_last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!s_last || tid >= 32) return;
     __threadfence();
-    w0 = w1 = 0.0;
+    double w0 = 0.0, w1 = 0.0;
     for (unsigned int j = tid; j < gridDim.x; j += 32) {
         w0 += __ldcg(A.partials + 2 * (size_t)j);
         w1 += __ldcg(A.partials + 2 * (size_t)j + 1);
@@ -219,10 +219,12 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
     const int nx = a.nx, ny = a.ny, N = (int)a.N;
     const float om = a.omega;
     const float w[9] = {a.w0, a.w1, a.w1, a.w1, a.w1, a.w2, a.w2, a.w2, a.w2};
-    // dJ/dG1, dJ/dG2: FP32 per thread over up to 16 sites, then FP64
+    // dJ/dG1, dJ/dG2: FP32 per thread over up to 16 sites, then FP64 (only when
+    // a thread has more than 16 sites)
     double g1 = 0.0, g2 = 0.0;
     float f1 = 0.f, f2 = 0.f;
     int nf = 0;
+    bool flushed = false;
     for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
         const int y = s / nx, x = s % nx;
         float f[9];
@@ -277,9 +279,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
             g2 += f2;
             f1 = f2 = 0.f;
             nf = 0;
+            flushed = true;
         }
     }
-    accumulate_grid2<kAdjThreads>(g1 + f1, g2 + f2, A);
+    if (flushed) {
+        f1 = (float)(g1 + f1);
+        f2 = (float)(g2 + f2);
+    }
+    accumulate_grid2<kAdjThreads>(f1, f2, A);
 }
 
 __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_b(const AdjArgs A)
