@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
         const float Sx = A.G1 * Swx + A.G2 * Spx, Sy = A.G1 * Swy + A.G2 * Spy;
         const float pc = a.psi_ref + p[2][2];
         const float Fx = -pc * Sx, Fy = -pc * Sy;
-        const float inv = 1.f / rho;
+        const float inv = __frcp_rn(rho);
         const float vx = fmaf(Fx, a.inv_omega, jx) * inv, vy = fmaf(Fy, a.inv_omega, jy) * inv;
         const float usq = vx * vx + vy * vy;
         // rho-bar gets omega sum_i l*_i feq_i / rho = omega sum_i l*_i w_i (1 + 3 c.v + ...);
