@@ -26,3 +26,22 @@ def test_c99_client_compiles_links_and_passes(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "abi_check: ok" in r.stdout
+
+
+@pytest.mark.gpu
+def test_c99_client_runs_a_lattice_on_the_gpu(tmp_path):
+    """tests/c/abi_run.c: init from host memory, 200 steps, trace, energy, fields,
+    save at t = 100 and resume, all through the C ABI."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib = libbuild.build()
+    exe = str(tmp_path / "abi_run")
+    cmd = [cc, "-std=c99", "-O2", "-Wall", "-Wextra", "-Werror", "-I" + os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "c", "abi_run.c"), "-L" + os.path.dirname(lib), "-llbsc",
+           "-Wl,-rpath," + os.path.dirname(lib), "-lm", "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "abi_run: ok" in r.stdout
