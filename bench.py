@@ -227,6 +227,70 @@ def run_adjoint(stream, dev, T=2000, n=512):
                         "(2 kernels per step), gradient w.r.t. rho_init, G1, G2"}
 
 
+def run_fp16(steps, warmup, stream, dev, peak):
+    """The same 8192^2 workload with the populations stored as FP16 deviations (44 B per
+    site: 18 B read + 18 B written + 4 + 4 B of psi), FP32 arithmetic: device-resident
+    MLUPS and the fraction of the copy bandwidth at 44 B/site."""
+    import torch
+
+    from paper_1008_2865_gb300 import Lattice, inputs, tune
+    rho0 = inputs.noisy_density(NX, NY, SEED, mean=0.7, amp=0.01, mode="rel")
+    with Lattice(rho0, omega=OMEGA, G1=G1, G2=G2, prec="fp16_delta", trace_every=TRACE_EVERY,
+                 device=dev, stream=stream.cuda_stream) as lat:
+        best = tune.lookup(NX, NY, "fp16_delta")
+        if best and len(best) == 3:
+            lat.set_launch(*best)
+        lat.step(warmup)
+        lat.step((-lat.t) % TRACE_EVERY)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        launch = lat.launch
+        e = lat.energy()
+        if not all(np.isfinite(e)):
+            raise RuntimeError(f"non-finite FP16-storage energies {e}")
+    gbs = 44 * NX * NY / (ms / 1e3) / 1e9
+    return {"workload": WORKLOAD.format(n=NX).replace("FP32 (deviation storage)",
+                                                      "FP16 deviation storage, FP32 arithmetic"),
+            "mlups": NX * NY / (ms / 1e3) / 1e6, "ms_per_step": ms, "steps": steps,
+            "launch": {"block_x": launch[0], "rows_per_cta": launch[1],
+                       "pipeline": ["register-prefetch", "bulk-copy rings"][launch[2]]},
+            "roofline": {"bound": "hbm", "bytes_per_site": 44, "achieved": gbs, "peak": peak,
+                         "unit": "GB/s", "frac": gbs / peak,
+                         "roof_mlups": peak * 1e9 / 44 / 1e6}}
+
+
+def run_step_split(stream, dev, launch, steps=20):
+    """Time of a plain step and of a step with the fused energy/mass reduction, each
+    timed over `steps` consecutive steps of the 8192^2 FP32 lattice (trace_every = 0
+    and 1), with the benchmark's launch shape."""
+    import torch
+
+    from paper_1008_2865_gb300 import Lattice, inputs
+    rho0 = inputs.noisy_density(NX, NY, SEED, mean=0.7, amp=0.01, mode="rel")
+    out = {}
+    for name, te in (("plain", 0), ("reduce", 1)):
+        with Lattice(rho0, omega=OMEGA, G1=G1, G2=G2, trace_every=te, device=dev,
+                     stream=stream.cuda_stream) as lat:
+            lat.set_launch(*launch)
+            lat.step(3)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            out[name + "_ms"] = e0.elapsed_time(e1) / steps
+    out["reduce_over_plain"] = out["reduce_ms"] / out["plain_ms"]
+    return out
+
+
 def cpu_baseline(seconds=12.0):
     """Oracle MLUPS on the host cores: a 512x512 lattice of the workload's parameters."""
     import oracle
@@ -370,6 +434,8 @@ def run_ours(args):
 
     batched = run_batched(args.steps, args.warmup, stream, dev) if not args.skip_batch else None
     adjoint = run_adjoint(stream, dev) if not args.skip_batch else None
+    fp16 = run_fp16(args.steps, args.warmup, stream, dev, peak) if not args.skip_batch else None
+    split = run_step_split(stream, dev, launch) if not args.skip_batch else None
 
     out = None
     if rank == 0:
@@ -404,6 +470,8 @@ def run_ours(args):
             "clocks": clocks,
             "batched": batched,
             "adjoint": adjoint,
+            "fp16_delta": fp16,
+            "step_split": split,
         }
     if ws > 1:
         import torch.distributed as dist
@@ -427,7 +495,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true",
                     help="time the device-resident steps only and print a short line")
     ap.add_argument("--skip-batch", action="store_true",
-                    help="leave out the batched 96-replica sweep and the adjoint workload")
+                    help="leave out the batched sweep, the adjoint, the FP16-storage run and "
+                         "the plain/reduce split")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

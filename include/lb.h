@@ -27,7 +27,13 @@
  *     that stream before they return and report what the kernels flagged
  *     since: LB_ERR_NONFINITE when a fused energy/mass reduction was not
  *     finite, LB_ERR_TIMEOUT when a bounded wait ran out.
- *   - Each call opens an NVTX range named after it (Nsight timelines).
+ *   - Each call that enqueues device work, synchronises or frees opens an NVTX
+ *     range named after it (Nsight timelines); the plain getters and setters
+ *     (lb_time, lb_get_launch, lb_set_launch, lb_set_wait_limit, lb_status_str,
+ *     lb_batch_count, lb_batch_time, lb_batch_get_launch) do not.
+ *   - The calling thread's current CUDA device is the same on return as it was
+ *     on entry: a call that works on a state of another device switches to that
+ *     device for its duration only.
  */
 #ifndef LBSC_LB_H
 #define LBSC_LB_H
@@ -145,11 +151,12 @@ lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta, int pipeline
  * (default 2e9, about one second at GB300 clocks). A wait that runs out makes
  * the kernel record an error and return; the next synchronising call
  * (lb_energy, lb_fields, lb_trace) reports LB_ERR_TIMEOUT and poisons the
- * state, while the CUDA context stays usable. extra_expect_bytes is a test
- * hook: when nonzero every row's barrier expects that many bytes more than
- * its copies deliver, so the waits run out on purpose; use 0 otherwise.
- * Errors: LB_ERR_ARG (NULL, cycles <= 0). */
-lb_status lb_set_wait_limit(lb_state* s, long long cycles, unsigned int extra_expect_bytes);
+ * state, while the CUDA context stays usable. test_skip_copies is a test hook
+ * (0 or 1): with 1, every CTA arms the barrier of its first row unit for the
+ * unit's bytes but issues none of the unit's copies, so that wait runs out on
+ * purpose with nothing of the unit in flight; use 0 otherwise.
+ * Errors: LB_ERR_ARG (NULL, cycles <= 0, test_skip_copies not 0 or 1). */
+lb_status lb_set_wait_limit(lb_state* s, long long cycles, int test_skip_copies);
 
 /* Guard check (debugging without a memory checker). Every device buffer of a
  * state is allocated with a 256-byte guard region on each side holding the
@@ -200,6 +207,20 @@ lb_status lb_load_state(lb_state* s, const void* src, size_t bytes);
 lb_status lb_adjoint(lb_state* s, long steps, const double* rho_target, int checkpoint_every,
                      double* J, double* grad_rho, double* grad_G);
 
+/* The objective of lb_adjoint evaluated on the current state, without the
+ * gradient: J = E_s + E_m + sum_x (rho(x) - rho_target(x))^2 (the Sec. 5
+ * pseudo-energy plus the squared density misfit), accumulated in FP64.
+ * For LB_FP32 (and LB_FP16_DELTA) states it runs lb_adjoint's own terminal
+ * kernel with the same grid and summation order, so lb_objective after
+ * lb_step(T) equals the J that lb_adjoint(T) returns, bit for bit; for LB_FP64
+ * states it evaluates the same sums on the FP64 populations.
+ *   rho_target  N doubles, host or device (pageable host memory goes through a
+ *               device buffer of N doubles that the state keeps, as in lb_fields)
+ *   J           host double
+ * Synchronises the stream. Errors: LB_ERR_ARG, LB_ERR_STATE, LB_ERR_OOM,
+ * LB_ERR_CUDA, LB_ERR_NONFINITE. */
+lb_status lb_objective(lb_state* s, const double* rho_target, double* J);
+
 /* ---- Batches: many independent lattices advanced by one launch per step ----
  * A batch holds `count` replicas (each with its own size, couplings, omega,
  * rho_ref and initial density; all with the same prec — LB_FP32 or
@@ -243,17 +264,20 @@ void lb_batch_destroy(lb_batch* b);
  * framework that hands out all device memory from its own pool (an extra
  * cudaMalloc there bypasses the pool's accounting and can fail once the pool
  * holds the memory), or code that must not trigger the implicit device
- * synchronisation of cudaMalloc. The sums are those of lb_energy:
- *   out[0] = E_s, out[1] = E_m, out[2] = E_bulk (Sec. 5), out[3] = sum rho,
+ * synchronisation of cudaMalloc. The sums are the same as lb_energy's:
+ *   out[0] = E_s, out[1] = E_m, out[2] = E_bulk, out[3] = sum rho,
  * computed from
  *   psi, rho  N = nx*ny doubles each, row-major [y][x], in device memory of
- *             the current device (the psi values are used as given);
+ *             the current device (the psi values are used as given); memory
+ *             of another device is refused with LB_ERR_ARG before any launch;
  *   nx, ny    >= 5, and nx*ny <= 134,217,728 sites (8192 CTAs of 16,384
  *             sites: the capacity of the scratch array below);
- *   G1, G2    the couplings of Eq. FORCE / Table 1;
+ *   G1, G2    the couplings, as for lb_init;
  *   out       4 doubles, host or device memory. With host memory the call
  *             synchronises the stream and returns LB_ERR_NONFINITE if a sum
  *             is not finite; with device memory it returns without waiting.
+ *             A host out while the stream is being captured is refused with
+ *             LB_ERR_ARG (the synchronisation would break the capture).
  * Scratch: one static device array of 262,208 bytes inside this library,
  * present on every GPU that loads the library until the process exits. The
  * first call on a device looks up that array's device address with the
@@ -262,8 +286,9 @@ void lb_batch_destroy(lb_batch* b);
  * clears its arrival counter first; calls whose kernels overlap on the GPU
  * (different streams, or different host threads on one device) race on it
  * and must be serialised by the caller.
- * Errors: LB_ERR_ARG (NULL, non-device psi/rho, sizes out of range,
- * non-finite couplings), LB_ERR_CUDA, LB_ERR_NONFINITE. */
+ * Errors: LB_ERR_ARG (NULL, psi/rho not in memory of the current device,
+ * sizes out of range, non-finite couplings, host out during capture),
+ * LB_ERR_CUDA, LB_ERR_NONFINITE. */
 lb_status lb_energy_noalloc(const double* psi, const double* rho, int nx, int ny, double G1,
                             double G2, double* out, void* stream);
 

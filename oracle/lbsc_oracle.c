@@ -511,7 +511,11 @@ double orc_objective(const orc_params* P, const double* rho_init, long steps,
     double* rho = (double*)malloc(sizeof(double) * N);
     double* psi = (double*)malloc(sizeof(double) * N);
     double* d = (double*)malloc(sizeof(double) * N);
-    if (orc_run(P, rho_init, steps, 0, rho, NULL, NULL, NULL, 0, NULL) != 0) return NAN;
+    if (!rho || !psi || !d ||
+        orc_run(P, rho_init, steps, 0, rho, NULL, NULL, NULL, 0, NULL) != 0) {
+        free(rho); free(psi); free(d);
+        return NAN;
+    }
     orc_psi(N, rho, P->rho0, psi);
     double g1, g2;
     const double E = energy_and_derivatives(P, psi, d, &g1, &g2);

@@ -13,7 +13,8 @@ from . import capi, inputs  # noqa: F401
 from .capi import (lb_batch_count, lb_batch_destroy, lb_batch_energy, lb_batch_fields,  # noqa: F401
                    lb_batch_get_launch, lb_batch_init, lb_batch_set_launch, lb_batch_step,
                    lb_batch_time, lb_batch_trace)
-from .capi import lb_adjoint, lb_load_state, lb_save_state, lb_state_bytes  # noqa: F401
+from .capi import (lb_adjoint, lb_load_state, lb_objective, lb_save_state,  # noqa: F401
+                   lb_state_bytes)
 from .capi import (LBError, lb_destroy, lb_energy, lb_fields, lb_get_launch,  # noqa: F401
                    lb_init, lb_set_launch, lb_set_wait_limit, lb_status_str, lb_step, lb_time,
                    lb_trace, make_params)
@@ -72,6 +73,10 @@ class Lattice:
         """(J, dJ/drho_init, (dJ/dG1, dJ/dG2)) of J = E_s(T) + E_m(T) + sum (rho(T) - rho*)^2
         over `steps` steps from this (fresh, FP32) state; leaves the state at t = steps."""
         return lb_adjoint(self.handle, steps, rho_target, checkpoint_every, grad_rho)
+
+    def objective(self, rho_target) -> float:
+        """J = E_s + E_m + sum (rho - rho*)^2 of the current state (the adjoint's objective)."""
+        return lb_objective(self.handle, rho_target)
 
     @property
     def launch(self):

@@ -7,12 +7,13 @@ J = E_s(T) + E_m(T) + sum_x (rho(x, T) - rho*(x))^2 after `steps` steps of the
 two-belt Shan–Chen lattice from f = w rho_init (FP32 state, FP64 gradient
 accumulation; see include/lb.h, lb_adjoint). When any input needs a gradient,
 the forward pass runs the library's checkpointed reverse sweep at once and
-keeps the gradients for backward; otherwise it only steps forward. All
-arithmetic runs in the library's CUDA kernels; torch only moves tensors.
+keeps the gradients for backward; otherwise it steps forward and evaluates J
+with lb_objective, the adjoint's own terminal kernel, so both paths give the
+same J bit for bit. All arithmetic runs in the library's CUDA kernels; torch
+only moves tensors.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import Lattice
@@ -32,12 +33,9 @@ class LBObjective(torch.autograd.Function):
                 J, _, gG = lat.adjoint(int(steps), tgt, checkpoint_every, grad_rho=grad)
                 ctx.save_for_backward(grad, torch.tensor(gG, dtype=torch.float64))
             else:
-                # J only: the library's energy of the final state plus the misfit
+                # J only: steps, then the adjoint's terminal sums on the device
                 lat.step(int(steps))
-                r = np.empty(tuple(rho.shape))
-                lat.fields(rho=r)
-                e = lat.energy()
-                J = e[0] + e[1] + float(((r - tgt.cpu().numpy()) ** 2).sum())
+                J = lat.objective(tgt)
         return torch.tensor(J, dtype=torch.float64, device=rho_init.device)
 
     @staticmethod

@@ -81,7 +81,7 @@ def load(build_if_missing: bool = False):
             lib.lb_get_launch.restype = ctypes.c_int
             lib.lb_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.lb_set_launch.restype = ctypes.c_int
-            lib.lb_set_wait_limit.argtypes = [vp, ctypes.c_longlong, ctypes.c_uint]
+            lib.lb_set_wait_limit.argtypes = [vp, ctypes.c_longlong, ctypes.c_int]
             lib.lb_set_wait_limit.restype = ctypes.c_int
             lib.lb_batch_init.argtypes = [ctypes.POINTER(vp), ctypes.c_int,
                                           ctypes.POINTER(lb_params), ctypes.POINTER(vp), vp]
@@ -121,6 +121,8 @@ def load(build_if_missing: bool = False):
             lib.lb_load_state.restype = ctypes.c_int
             lib.lb_adjoint.argtypes = [vp, ctypes.c_long, vp, ctypes.c_int, dp, vp, dp]
             lib.lb_adjoint.restype = ctypes.c_int
+            lib.lb_objective.argtypes = [vp, vp, dp]
+            lib.lb_objective.restype = ctypes.c_int
             lib.lb_energy_noalloc.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_double, ctypes.c_double, vp, vp]
             lib.lb_energy_noalloc.restype = ctypes.c_int
@@ -214,8 +216,8 @@ def lb_set_launch(h: int, block_x: int, rows_per_cta: int, pipeline: int) -> Non
                                 int(pipeline)), "lb_set_launch")
 
 
-def lb_set_wait_limit(h: int, cycles: int, extra_expect_bytes: int = 0) -> None:
-    _check(load().lb_set_wait_limit(ctypes.c_void_p(h), int(cycles), int(extra_expect_bytes)),
+def lb_set_wait_limit(h: int, cycles: int, test_skip_copies: int = 0) -> None:
+    _check(load().lb_set_wait_limit(ctypes.c_void_p(h), int(cycles), int(test_skip_copies)),
            "lb_set_wait_limit")
 
 
@@ -281,6 +283,17 @@ def lb_adjoint(h: int, steps: int, rho_target, checkpoint_every: int = 0, grad_r
                              int(checkpoint_every), ctypes.byref(J), _ptr(out), gG),
            "lb_adjoint")
     return float(J.value), out, (float(gG[0]), float(gG[1]))
+
+
+def lb_objective(h: int, rho_target) -> float:
+    """J = E_s + E_m + sum (rho - rho_target)^2 of the current state (FP64 sums on the
+    device; for FP32 states the same kernel and order as lb_adjoint's J)."""
+    if isinstance(rho_target, np.ndarray):
+        rho_target = np.ascontiguousarray(rho_target, dtype=np.float64)
+    J = ctypes.c_double(0.0)
+    _check(load().lb_objective(ctypes.c_void_p(h), _ptr(rho_target), ctypes.byref(J)),
+           "lb_objective")
+    return float(J.value)
 
 
 def lb_batch_init(params_list, rho_list, stream: int = 0) -> int:

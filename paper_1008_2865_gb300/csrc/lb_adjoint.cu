@@ -27,8 +27,6 @@
 #include <new>
 #include <vector>
 
-#include <nvtx3/nvToolsExt.h>
-
 #include "lb_device.cuh"
 
 using namespace lbsc;
@@ -84,7 +82,8 @@ __host__ __device__ constexpr int cy_of(int i)
 }
 
 // Deviations f_i(x, y) - w_i rho_ref of state t, read from the tiled populations.
-__device__ __forceinline__ void site_f(const float* __restrict__ g, int pitch, int x, int y,
+template <typename T>
+__device__ __forceinline__ void site_f(const T* __restrict__ g, int pitch, int x, int y,
                                        float f[9])
 {
     load_site(f, g + y * pitch + tcol(x));
@@ -173,7 +172,11 @@ __device__ void accumulate_grid2(float v0, float v1, const AdjArgs& A)
     }
 }
 
-__global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A)
+// J of the state (A.g / gT, A.dpsi) and the terminal adjoint l(T) (skipped when
+// A.lam is null: lb_objective). T is the population storage type.
+template <typename T>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A,
+                                                              const T* __restrict__ gT)
 {
     const StepArgs<float>& a = A.a;
     const int nx = a.nx, ny = a.ny, N = (int)a.N;
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A)
     for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
         const int y = s / nx, x = s % nx;
         float f[9];
-        site_f(A.g, a.pitch, x, y, f);
+        site_f(gT, a.pitch, x, y, f);
         const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
         const float rho = a.rho_ref + d;
         const Nbr5 nb = nbr5(x, y, nx, ny);
@@ -202,9 +205,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A)
                          A.ap.K5 * S5 + A.ap.K8 * S8;
         const float dpr = __expf(-rho * a.inv_rho0) * A.inv_sqrt_rho0;
         const double mis = (double)rho - A.rho_target[s];
-        const float lam = dpr * dEdpsi + (float)(2.0 * mis);
+        if (A.lam) {
+            const float lam = dpr * dEdpsi + (float)(2.0 * mis);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) A.lam[i * N + s] = lam;
+            for (int i = 0; i < 9; ++i) A.lam[i * N + s] = lam;
+        }
         v[0] += 0.5 * (double)pc * dEdpsi;
         v[1] += mis * mis;
         v[2] += 0.5 * (double)pc * sw;
@@ -366,16 +371,13 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
                                 int checkpoint_every, double* J_out, double* grad_rho,
                                 double* grad_G)
 {
-    nvtxRangePushA("lb_adjoint");
-    struct PopRange { ~PopRange() { nvtxRangePop(); } } pop_range;
+    NvtxRange nvtx_range("lb_adjoint");
     if (!s || steps < 0 || !rho_target || !J_out || !grad_rho || !grad_G || checkpoint_every < 0)
         return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;
     if (s->p.prec != LB_FP32 || s->t != 0) return LB_ERR_STATE;
-    if (cudaSetDevice(s->p.device) != cudaSuccess) {
-        cudaGetLastError();
-        return LB_ERR_CUDA;
-    }
+    DeviceScope dev(s->p.device);
+    if (!dev.ok) return LB_ERR_CUDA;
     const int N = (int)s->N;
     const long long T = steps;
     long long C = checkpoint_every > 0 ? checkpoint_every : (long long)std::ceil(std::sqrt((double)T));
@@ -463,7 +465,7 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
     A.dpsi = s->dpsi[s->cur];
     A.lam = lamA;
     A.acc = acc;             // acc[0..3] = E, misfit, dE/dG1, dE/dG2
-    k_adj_terminal<<<grid, kAdjThreads, 0, st>>>(A);
+    k_adj_terminal<float><<<grid, kAdjThreads, 0, st>>>(A, A.g);
     if (cudaGetLastError() != cudaSuccess) return fail();
 
     // ---- reverse over the segments, recomputing each from its checkpoint
@@ -517,3 +519,58 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
         return LB_ERR_NONFINITE;
     return LB_OK;
 }
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_misfit64(const double* __restrict__ rho,
+                                                  const double* __restrict__ tgt, long long n,
+                                                  double* partials, unsigned int* counter,
+                                                  double* out)
+{
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long s = blockIdx.x * 256LL + threadIdx.x; s < n; s += (long long)gridDim.x * 256) {
+        const double m = rho[s] - tgt[s];
+        v[0] += m * m;
+    }
+    if (last_block_total<256>(v, partials, counter, gridDim.x)) *out = v[0];
+}
+
+}  // namespace
+
+namespace lbsc {
+
+cudaError_t objective_delta(const lb_state* s, const double* tgt, double* acc, cudaStream_t st)
+{
+    AdjArgs A{};
+    A.a = state_args<float>(s, s->cur);
+    A.aw = with_weights(A.a, false);
+    A.ap = with_weights(A.a, true);
+    A.G1 = (float)s->p.G1;
+    A.G2 = (float)s->p.G2;
+    A.inv_sqrt_rho0 = (float)(1.0 / std::sqrt(s->p.rho0));
+    A.dpsi = s->dpsi[s->cur];
+    A.rho_target = tgt;
+    A.partials = s->partials;
+    A.counter = s->counter;
+    A.acc = acc;
+    A.lam = nullptr;
+    cudaError_t e = cudaMemsetAsync(acc, 0, 4 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int grid = adj_grid(s->N);
+    if (s->p.prec == LB_FP16_DELTA)
+        k_adj_terminal<__half><<<grid, kAdjThreads, 0, st>>>(A, static_cast<const __half*>(s->g[s->cur]));
+    else
+        k_adj_terminal<float><<<grid, kAdjThreads, 0, st>>>(A, static_cast<const float*>(s->g[s->cur]));
+    return cudaGetLastError();
+}
+
+cudaError_t misfit64(const double* rho, const double* tgt, long long n, double* partials,
+                     unsigned int* counter, double* out, cudaStream_t st)
+{
+    long long b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    k_misfit64<<<(int)(b < 1 ? 1 : b), 256, 0, st>>>(rho, tgt, n, partials, counter, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbsc

@@ -8,19 +8,9 @@
 #include <new>
 #include <vector>
 
-#include <nvtx3/nvToolsExt.h>
-
 #include "lb_internal.h"
 
 using namespace lbsc;
-
-namespace {
-// NVTX range for the duration of an ABI call (visible in Nsight timelines).
-struct NvtxRange {
-    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
-    ~NvtxRange() { nvtxRangePop(); }
-};
-}  // namespace
 
 namespace lbsc {
 
@@ -69,10 +59,6 @@ Couplings couplings(double G1, double G2)
     return c;
 }
 
-}  // namespace lbsc
-
-namespace {
-
 // Where a kernel can read or write an array directly: device (or managed) memory
 // as it is, pinned host memory through its device alias (read or written over
 // the host link by the kernel, no staging copy); nullptr for pageable host memory.
@@ -89,6 +75,10 @@ double* device_view(double* p)
         return static_cast<double*>(at.devicePointer);
     return nullptr;
 }
+
+}  // namespace lbsc
+
+namespace {
 
 lb_status validate(const lb_params* p)
 {
@@ -187,7 +177,7 @@ StepArgs<T> state_args(const lb_state* s, int cur)
     a.t = s->t;
     a.err = s->err;
     a.wait_cycles = s->wait_cycles;
-    a.extra_tx = s->extra_tx;
+    a.skip_unit0 = s->skip_unit0;
     return a;
 }
 
@@ -233,7 +223,7 @@ lb_status check_err(lb_state* s)
 void free_state(lb_state* s)
 {
     if (!s) return;
-    cudaSetDevice(s->p.device);
+    DeviceScope dev(s->p.device);
     cudaStreamSynchronize(s->stream);
     for (const lb_state::Alloc& a : s->allocs) cudaFree(a.base);
     cudaGetLastError();
@@ -320,8 +310,8 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
     s->stream = static_cast<cudaStream_t>(stream);
     s->N = (long long)p->nx * p->ny;
     const long long N = s->N;
-    if (cudaSetDevice(p->device) != cudaSuccess) {
-        cudaGetLastError();
+    DeviceScope dev(p->device);
+    if (!dev.ok) {
         delete s;
         return LB_ERR_CUDA;
     }
@@ -428,7 +418,8 @@ lb_status lb_step(lb_state* s, long n)
     if (!s || n < 0) return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;
     if (n == 0) return LB_OK;
-    LB_CUDA(s, cudaSetDevice(s->p.device));
+    DeviceScope dev(s->p.device);
+    if (!dev.ok) return fail_cuda(s);
     return s->p.prec == LB_FP64 ? step_fp64(s, n) : step_fp32(s, n);
 }
 
@@ -437,7 +428,8 @@ lb_status lb_energy(lb_state* s, double out[4])
     NvtxRange nvtx_range("lb_energy");
     if (!s || !out) return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;
-    LB_CUDA(s, cudaSetDevice(s->p.device));
+    DeviceScope dev(s->p.device);
+    if (!dev.ok) return fail_cuda(s);
     if (s->p.prec == LB_FP64) {
         const Fp64Args a = make64(s);
         LB_CUDA(s, fp64_psi(a, s->stream));
@@ -465,6 +457,55 @@ lb_status lb_energy(lb_state* s, double out[4])
     return LB_OK;
 }
 
+lb_status lb_objective(lb_state* s, const double* rho_target, double* J)
+{
+    NvtxRange nvtx_range("lb_objective");
+    if (!s || !rho_target || !J) return LB_ERR_ARG;
+    if (s->poisoned) return LB_ERR_STATE;
+    DeviceScope dev(s->p.device);
+    if (!dev.ok) return fail_cuda(s);
+    const long long N = s->N;
+    // the target where a kernel can read it: in place, or copied into the
+    // state's field buffer (allocated on first use, as by lb_fields)
+    const double* tgt = device_view(const_cast<double*>(rho_target));
+    if (!tgt) {
+        if (!s->field_tmp) {
+            s->field_tmp = static_cast<double*>(state_alloc(s, sizeof(double) * N));
+            if (!s->field_tmp) return LB_ERR_OOM;
+        }
+        LB_CUDA(s, cudaMemcpyAsync(s->field_tmp, rho_target, sizeof(double) * N,
+                                   cudaMemcpyHostToDevice, s->stream));
+        tgt = s->field_tmp;
+    }
+    double h[4] = {0.0, 0.0, 0.0, 0.0};
+    if (s->p.prec == LB_FP64) {
+        // psi and rho of the current state, the Sec. 5 sums, then the misfit
+        const Fp64Args a = make64(s);
+        LB_CUDA(s, fp64_psi(a, s->stream));
+        LB_CUDA(s, fp64_energy(a, s->partials, s->counter, s->res, nullptr, nullptr, s->t,
+                               s->stream));
+        LB_CUDA(s, cudaMemcpyAsync(h, s->res, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                   s->stream));
+        LB_CUDA(s, misfit64(s->rho64, tgt, N, s->partials, s->counter, s->res, s->stream));
+        LB_CUDA(s, cudaMemcpyAsync(h + 2, s->res, sizeof(double), cudaMemcpyDeviceToHost,
+                                   s->stream));
+        LB_CUDA(s, cudaStreamSynchronize(s->stream));
+        *J = (h[0] + h[1]) + h[2];
+    } else {
+        // the terminal sums of lb_adjoint (same kernel, grid and order)
+        LB_CUDA(s, objective_delta(s, tgt, s->res, s->stream));
+        LB_CUDA(s, cudaMemcpyAsync(h, s->res, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                   s->stream));
+        LB_CUDA(s, cudaStreamSynchronize(s->stream));
+        *J = h[0] + h[1];
+    }
+    {
+        const lb_status st = check_err(s);
+        if (st != LB_OK) return st;
+    }
+    return std::isfinite(*J) ? LB_OK : LB_ERR_NONFINITE;
+}
+
 static cudaError_t fields_into(lb_state* s, double* r, double* x, double* y)
 {
     if (s->p.prec == LB_FP64) return fp64_fields(s->f64[s->cur], s->p.nx, s->p.ny, r, x, y, s->stream);
@@ -480,7 +521,8 @@ lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy)
     NvtxRange nvtx_range("lb_fields");
     if (!s) return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;
-    LB_CUDA(s, cudaSetDevice(s->p.device));
+    DeviceScope dev(s->p.device);
+    if (!dev.ok) return fail_cuda(s);
     const long long N = s->N;
     double* outs[3] = {rho, ux, uy};
     double* views[3];
@@ -513,9 +555,11 @@ lb_status lb_fields(lb_state* s, double* rho, double* ux, double* uy)
 
 lb_status lb_trace(lb_state* s, double* buf, int cap, int* count)
 {
+    NvtxRange nvtx_range("lb_trace");
     if (!s || !count || cap < 0 || (cap > 0 && !buf)) return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;
-    LB_CUDA(s, cudaSetDevice(s->p.device));
+    DeviceScope dev(s->p.device);
+    if (!dev.ok) return fail_cuda(s);
     int total = 0;
     LB_CUDA(s, cudaMemcpyAsync(&total, s->trace_count, sizeof(int), cudaMemcpyDeviceToHost,
                                s->stream));
@@ -560,9 +604,11 @@ size_t payload_bytes(const lb_state* s)
 
 lb_status lb_check_guards(lb_state* s, int* damaged)
 {
+    NvtxRange nvtx_range("lb_check_guards");
     if (!s || !damaged) return LB_ERR_ARG;
     *damaged = 0;
-    LB_CUDA(s, cudaSetDevice(s->p.device));
+    DeviceScope dev(s->p.device);
+    if (!dev.ok) return fail_cuda(s);
     LB_CUDA(s, cudaStreamSynchronize(s->stream));
     std::vector<unsigned char> h(2 * kGuardBytes);
     for (const lb_state::Alloc& a : s->allocs) {
@@ -586,8 +632,10 @@ void lb_debug_fail_alloc(int after)
 
 lb_status lb_debug_damage_guard(lb_state* s, int buffer)
 {
+    NvtxRange nvtx_range("lb_debug_damage_guard");
     if (!s || buffer < 0 || buffer >= (int)s->allocs.size()) return LB_ERR_ARG;
-    LB_CUDA(s, cudaSetDevice(s->p.device));
+    DeviceScope dev(s->p.device);
+    if (!dev.ok) return fail_cuda(s);
     const lb_state::Alloc& a = s->allocs[(size_t)buffer];
     char* tail = static_cast<char*>(a.base) + kGuardBytes + a.bytes;
     LB_CUDA(s, cudaMemsetAsync(tail + 17, 0x00, 1, s->stream));
@@ -602,9 +650,11 @@ size_t lb_state_bytes(const lb_state* s)
 
 lb_status lb_save_state(lb_state* s, void* dst, size_t bytes)
 {
+    NvtxRange nvtx_range("lb_save_state");
     if (!s || !dst || bytes < lb_state_bytes(s)) return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;
-    LB_CUDA(s, cudaSetDevice(s->p.device));
+    DeviceScope dev(s->p.device);
+    if (!dev.ok) return fail_cuda(s);
     SavedHeader h{};
     std::memcpy(h.magic, "LBSCSTAT", 8);
     h.version = kSaveVersion;
@@ -631,9 +681,11 @@ lb_status lb_save_state(lb_state* s, void* dst, size_t bytes)
 
 lb_status lb_load_state(lb_state* s, const void* src, size_t bytes)
 {
+    NvtxRange nvtx_range("lb_load_state");
     if (!s || !src || bytes < sizeof(SavedHeader)) return LB_ERR_ARG;
     if (s->poisoned) return LB_ERR_STATE;
-    LB_CUDA(s, cudaSetDevice(s->p.device));
+    DeviceScope dev(s->p.device);
+    if (!dev.ok) return fail_cuda(s);
     SavedHeader h{};
     LB_CUDA(s, cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDefault, s->stream));
     LB_CUDA(s, cudaStreamSynchronize(s->stream));
@@ -689,16 +741,20 @@ lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta, int pipeline
     return LB_OK;
 }
 
-lb_status lb_set_wait_limit(lb_state* s, long long cycles, unsigned int extra_expect_bytes)
+lb_status lb_set_wait_limit(lb_state* s, long long cycles, int test_skip_copies)
 {
-    if (!s || cycles <= 0) return LB_ERR_ARG;
+    if (!s || cycles <= 0 || (test_skip_copies != 0 && test_skip_copies != 1)) return LB_ERR_ARG;
     s->wait_cycles = cycles;
-    s->extra_tx = extra_expect_bytes;
+    s->skip_unit0 = test_skip_copies;
     return LB_OK;
 }
 
 long lb_time(const lb_state* s) { return s ? (long)s->t : -1; }
 
-void lb_destroy(lb_state* s) { free_state(s); }
+void lb_destroy(lb_state* s)
+{
+    NvtxRange nvtx_range("lb_destroy");
+    free_state(s);
+}
 
 }  // extern "C"

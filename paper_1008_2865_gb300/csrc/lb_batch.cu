@@ -8,8 +8,6 @@
 #include <new>
 #include <vector>
 
-#include <nvtx3/nvToolsExt.h>
-
 #include "lb_internal.h"
 
 using namespace lbsc;
@@ -171,6 +169,7 @@ extern "C" {
 lb_status lb_batch_init(lb_batch** out, int count, const lb_params* params,
                         const double* const* rho_init, void* stream)
 {
+    NvtxRange nvtx_range("lb_batch_init");
     if (!out) return LB_ERR_ARG;
     *out = nullptr;
     if (count < 1 || !params || !rho_init) return LB_ERR_ARG;
@@ -198,7 +197,8 @@ lb_status lb_batch_init(lb_batch** out, int count, const lb_params* params,
         b->reps.push_back(s);
         b->om1 = b->om1 && params[r].omega == 1.0;
     }
-    if (cudaSetDevice(b->device) != cudaSuccess ||
+    DeviceScope dev(b->device);
+    if (!dev.ok ||
         cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device) !=
             cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -220,11 +220,11 @@ lb_status lb_batch_init(lb_batch** out, int count, const lb_params* params,
 
 lb_status lb_batch_step(lb_batch* b, long n)
 {
-    nvtxRangePushA("lb_batch_step");
-    struct PopRange { ~PopRange() { nvtxRangePop(); } } pop_range;
+    NvtxRange nvtx_range("lb_batch_step");
     if (!b || n < 0) return LB_ERR_ARG;
     if (b->poisoned) return LB_ERR_STATE;
-    if (cudaSetDevice(b->device) != cudaSuccess) return poison(b);
+    DeviceScope dev(b->device);
+    if (!dev.ok) return poison(b);
     while (n > 0) {
         if (b->use_graph && b->period > 0 && b->t % b->period == 0 && n >= b->period &&
             build_graph(b)) {
@@ -283,8 +283,9 @@ lb_status lb_batch_set_launch(lb_batch* b, int block_x, int rows_per_cta, int us
         return LB_ERR_ARG;
     if (rows_per_cta < kMinRows || rows_per_cta > kMaxRows || (use_graph != 0 && use_graph != 1))
         return LB_ERR_ARG;
-    if (cudaSetDevice(b->device) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess)
-        return poison(b);
+    NvtxRange nvtx_range("lb_batch_set_launch");
+    DeviceScope dev(b->device);
+    if (!dev.ok || cudaStreamSynchronize(b->stream) != cudaSuccess) return poison(b);
     b->block_x = block_x;
     b->rows = rows_per_cta;
     b->use_graph = use_graph == 1;
@@ -311,7 +312,8 @@ long lb_batch_time(const lb_batch* b) { return b ? (long)b->t : -1; }
 void lb_batch_destroy(lb_batch* b)
 {
     if (!b) return;
-    cudaSetDevice(b->device);
+    NvtxRange nvtx_range("lb_batch_destroy");
+    DeviceScope dev(b->device);
     cudaStreamSynchronize(b->stream);
     free_tables(b);
     if (b->cap) cudaStreamDestroy(b->cap);

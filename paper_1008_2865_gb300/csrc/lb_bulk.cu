@@ -28,7 +28,10 @@
 // Every wait on an mbarrier is bounded by a clock limit; a CTA whose wait
 // runs out sets the state's error flag and all its threads leave together at
 // the next per-row barrier (__syncthreads_or), after a bounded wait for the
-// copies they issued. No wait in this file can spin forever.
+// copies they issued. No wait in this file can spin forever. The test hook of
+// lb_set_wait_limit arms unit 0's barrier and issues none of its copies: that
+// wait runs out with no copy of the unit in flight, and the units issued
+// before the timeout complete before the CTA leaves.
 #include "lb_device.cuh"
 
 #include <cstdint>
@@ -162,18 +165,20 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
     const int xc = x0 - 1 + tid;                 // output column (out_col threads)
     const int cx = tcol(xc);
     const long long limit = a.wait_cycles;
-    const uint32_t unit_bytes =
-        (uint32_t)(nt * kTileElems * sizeof(T) + WP * sizeof(float)) + a.extra_tx;
+    const uint32_t unit_bytes = (uint32_t)(nt * kTileElems * sizeof(T) + WP * sizeof(float));
 
     // ---- producer: lanes 0..2 of warp 0 issue the copies of one unit
     auto issue_unit = [&](int j) {
         const int lane = tid;                    // only called by warp 0
         uint64_t* bar = &bars[j < 0 ? NB : j % NB];
         if (lane == 0) {
-            const uint32_t bytes = j < 0 ? 4u * WP * sizeof(float) + a.extra_tx : unit_bytes;
+            const uint32_t bytes = j < 0 ? 4u * WP * sizeof(float) : unit_bytes;
             mbar_arrive_expect_tx(bar, bytes);
         }
         __syncwarp();
+        // test hook: unit 0's barrier is armed for its bytes but none of its copies
+        // is issued, so its wait runs out while nothing of that unit is in flight
+        if (a.skip_unit0 && j == 0) return;
         if (j < 0) {
             // the four leading dpsi rows y0-3 .. y0
             if (lane < 4) {

@@ -8,9 +8,47 @@
 #include <cstdint>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lb.h"
 
 namespace lbsc {
+
+// NVTX range for the duration of an ABI call (visible in Nsight timelines).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Makes `dev` the calling thread's current device for the duration of an ABI
+// call and gives the caller's current device back on return, so that a call on
+// a state of another device does not move the caller's thread (a torch caller
+// working on device 1 stays on device 1). ok is false if the switch failed.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceScope(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+    ~DeviceScope()
+    {
+        int now = -1;
+        if (prev >= 0 && (cudaGetDevice(&now) != cudaSuccess || now != prev)) {
+            cudaSetDevice(prev);
+            cudaGetLastError();
+        }
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+};
 
 constexpr int kTraceCap = 65536;     // rows kept in the device trace ring
 constexpr int kTraceCols = 5;        // (t, mass, E_s, E_m, E_bulk)
@@ -62,7 +100,7 @@ struct StepArgs {
     // bounded waits of the bulk-copy kernel
     int* err;                        // error flags: 1 a wait ran out, 2 a reduction was not finite
     long long wait_cycles;           // clock limit of one wait
-    unsigned int extra_tx;           // test hook: bytes a unit's barrier expects beyond its copies
+    int skip_unit0;                  // test hook: the first row unit's barrier is armed, no copy issued
 };
 
 // Output rows per CTA accepted by lb_set_launch / lb_batch_set_launch.
@@ -161,7 +199,7 @@ struct lb_state {
     lbsc::Fp32Launch launch{128, 64, 0};
     int* err = nullptr;            // set by a kernel whose bounded wait ran out
     long long wait_cycles = 2000000000LL;
-    unsigned int extra_tx = 0;
+    int skip_unit0 = 0;            // test hook of lb_set_wait_limit
     // FP64 parity storage
     double* f64[2] = {nullptr, nullptr};
     double* psi64 = nullptr;
@@ -195,4 +233,14 @@ namespace lbsc {
 template <typename T>
 StepArgs<T> state_args(const lb_state* s, int cur);   // arguments of a step from buffers `cur`
 size_t elem_size(lb_precision p);
+// Where a kernel can read or write a double array directly: device memory as it
+// is, pinned host memory through its device alias; nullptr for pageable memory.
+double* device_view(double* p);
+// Objective sums of lb_adjoint's terminal kernel for an FP32/FP16 state
+// (lb_adjoint.cu): acc[0] = E_s + E_m of the current state, acc[1] = sum (rho -
+// tgt)^2, acc[2..3] the explicit dE/dG1, dE/dG2; tgt is device memory.
+cudaError_t objective_delta(const lb_state* s, const double* tgt, double* acc, cudaStream_t st);
+// *out = sum (rho - tgt)^2 over n doubles in device memory, deterministic.
+cudaError_t misfit64(const double* rho, const double* tgt, long long n, double* partials,
+                     unsigned int* counter, double* out, cudaStream_t st);
 }  // namespace lbsc

@@ -101,15 +101,18 @@ k_energy_noalloc(const double* __restrict__ psi, const double* __restrict__ rho,
     }
 }
 
-bool is_device_ptr(const void* p)
+// Device ordinal of device (or managed) memory p; -1 for host memory, an
+// unknown pointer or NULL.
+int device_of(const void* p)
 {
-    if (!p) return false;
+    if (!p) return -1;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return -1;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return at.device;
+    return -1;
 }
 
 // The device address of the scratch array on the current device (looked up
@@ -135,21 +138,35 @@ extern "C" lb_status lb_energy_noalloc(const double* psi, const double* rho, int
                                        double G1, double G2, double* out, void* stream)
 {
     using namespace lbsc;
+    NvtxRange nvtx_range("lb_energy_noalloc");
     if (!psi || !rho || !out) return LB_ERR_ARG;
     if (nx < 5 || ny < 5) return LB_ERR_ARG;
     if (!std::isfinite(G1) || !std::isfinite(G2)) return LB_ERR_ARG;
     const long long N = (long long)nx * ny;
     const long long ctas = (N + kNoAllocSitesPerCta - 1) / kNoAllocSitesPerCta;
     if (ctas > kNoAllocMaxCtas) return LB_ERR_ARG;   // more sites than the scratch array covers
-    if (!is_device_ptr(psi) || !is_device_ptr(rho)) return LB_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
         return LB_ERR_CUDA;
     }
+    // the fields must live on the current device (the kernel reads them there)
+    if (device_of(psi) != dev || device_of(rho) != dev) return LB_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int out_dev = device_of(out);
+    if (out_dev >= 0 && out_dev != dev) return LB_ERR_ARG;
+    const bool dev_out = out_dev == dev;
+    if (!dev_out) {
+        // a host result needs a stream synchronisation, which a capture forbids
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return LB_ERR_CUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return LB_ERR_ARG;
+    }
     double* scratch = scratch_address(dev);
     if (!scratch) return LB_ERR_CUDA;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Couplings K = couplings(G1, G2);
     // the arrival counter must start at zero; the partials are overwritten
     if (cudaMemsetAsync(scratch, 0, sizeof(double), st) != cudaSuccess) {
@@ -159,7 +176,6 @@ extern "C" lb_status lb_energy_noalloc(const double* psi, const double* rho, int
     k_energy_noalloc<<<(unsigned int)ctas, kNoAllocThreads, 0, st>>>(
         psi, rho, nx, ny, K.K0, K.K1, K.K2, K.K4, K.K5, K.K8, 0.5 * (G1 + G2), scratch);
     if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
-    const bool dev_out = is_device_ptr(out);
     if (cudaMemcpyAsync(out, scratch + 4, 4 * sizeof(double),
                         dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         st) != cudaSuccess) {

@@ -327,13 +327,16 @@ def test_pipeline_availability():
 
 
 def test_bounded_wait_reports_timeout_and_context_survives():
-    """A barrier that expects bytes no copy delivers makes every wait run out; the
-    kernel returns, the next synchronising call reports LB_ERR_TIMEOUT, and the
-    CUDA context keeps working for a fresh state."""
+    """Every CTA arms the barrier of its first row unit and issues none of that unit's
+    copies (test hook), so that wait runs out with nothing of the unit in flight; the
+    kernel returns, the next synchronising call reports LB_ERR_TIMEOUT, and the CUDA
+    context keeps working for a fresh state."""
     rho0 = inputs.noisy_density(256, 48, seed=2)
     lat = Lattice(rho0, trace_every=0)
     lat.set_launch(128, 16, 1)
-    capi.lb_set_wait_limit(lat.handle, 2_000_000, 16)    # ~1 ms per wait
+    with pytest.raises(LBError):
+        capi.lb_set_wait_limit(lat.handle, 2_000_000, 2)  # the hook takes 0 or 1
+    capi.lb_set_wait_limit(lat.handle, 2_000_000, 1)     # ~1 ms per wait
     lat.step(1)
     with pytest.raises(LBError) as ei:
         lat.energy()
