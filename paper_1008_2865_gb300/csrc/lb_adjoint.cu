@@ -111,6 +111,16 @@ struct AdjArgs {
     double* acc;              // [4] FP64 accumulators
 };
 
+// s += x with Kahan's compensation c (the rounding error of the previous adds).
+// The operations must not be reassociated: nvcc does not, and fmaf is not used.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x)
+{
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
 template <int NT>
 __device__ void accumulate_grid(double v[4], const AdjArgs& A)
 {
@@ -120,54 +130,68 @@ __device__ void accumulate_grid(double v[4], const AdjArgs& A)
     }
 }
 
-// Grid sum of two per-thread values added into A.acc[0..1] with as little FP64
-// work as possible (FP64 issues slowly on this part): a fixed FP32 shuffle tree
-// in each warp, the warp sums converted to FP64 and added by warp 0 in a fixed
-// order, and the last block to finish sums the block partials in block order.
+// Grid sum of two per-thread values added into A.acc[0..1] with little FP64
+// work (FP64 issues slowly on this part) and no long dependent chains: the
+// CTA's values meet in shared memory, each lane of warp 0 adds NT/32 of them in
+// FP32 in a fixed order, the 32 lane sums go to FP64 and a fixed shuffle tree
+// adds them; the last CTA to finish sums the CTA partials in FP64 in CTA order
+// (loads issued four at a time). Error: each FP32 lane sum adds at most NT/32
+// per-thread values, so its relative error is below (NT/32) 2^-24 of the sum of
+// their magnitudes; everything above it is FP64.
 template <int NT>
 __device__ void accumulate_grid2(float v0, float v1, const AdjArgs& A)
 {
-    constexpr int NW = NT / 32;
-    __shared__ float sh[2][NW];
+    __shared__ float sh[2][NT];
     __shared__ bool s_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
+    sh[0][tid] = v0;
+    sh[1][tid] = v1;
+    __syncthreads();
+    if (tid < 32) {
+        float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        v0 += __shfl_down_sync(0xffffffffu, v0, o);
-        v1 += __shfl_down_sync(0xffffffffu, v1, o);
-    }
-    if (lane == 0) {
-        sh[0][warp] = v0;
-        sh[1][warp] = v1;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double w0 = 0.0, w1 = 0.0;
-        for (int k = 0; k < NW; ++k) {
-            w0 += (double)sh[0][k];
-            w1 += (double)sh[1][k];
+        for (int k = tid; k < NT; k += 32) {
+            a0 += sh[0][k];
+            a1 += sh[1][k];
         }
-        A.partials[2 * (size_t)blockIdx.x] = w0;
-        A.partials[2 * (size_t)blockIdx.x + 1] = w1;
-        __threadfence();
-        s_last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
+        double w0 = a0, w1 = a1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w0 += __shfl_down_sync(0xffffffffu, w0, o);
+            w1 += __shfl_down_sync(0xffffffffu, w1, o);
+        }
+        if (tid == 0) {
+            reinterpret_cast<double2*>(A.partials)[blockIdx.x] = make_double2(w0, w1);
+            __threadfence();
+            s_last = atomicAdd(A.counter, 1u) == gridDim.x - 1;
+        }
     }
     __syncthreads();
-    if (!s_last || tid >= 32) return;
+    if (!s_last) return;
     __threadfence();
     double w0 = 0.0, w1 = 0.0;
-    for (unsigned int j = tid; j < gridDim.x; j += 32) {
-        w0 += __ldcg(A.partials + 2 * (size_t)j);
-        w1 += __ldcg(A.partials + 2 * (size_t)j + 1);
-    }
+    const double2* p2 = reinterpret_cast<const double2*>(A.partials);
+    unsigned int j = tid;
+    for (; j + 3 * NT < gridDim.x; j += 4 * NT) {
+        double2 q[4];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        w0 += __shfl_down_sync(0xffffffffu, w0, o);
-        w1 += __shfl_down_sync(0xffffffffu, w1, o);
+        for (int u = 0; u < 4; ++u) q[u] = __ldcg(p2 + j + u * NT);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            w0 += q[u].x;
+            w1 += q[u].y;
+        }
     }
+    for (; j < gridDim.x; j += NT) {
+        const double2 q = __ldcg(p2 + j);
+        w0 += q.x;
+        w1 += q.y;
+    }
+    double v[4] = {w0, w1, 0.0, 0.0};
+    block_sum4<NT>(v);
     if (tid == 0) {
-        A.acc[0] += w0;
-        A.acc[1] += w1;
+        A.acc[0] += v[0];
+        A.acc[1] += v[1];
         *A.counter = 0u;
     }
 }
@@ -224,12 +248,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
     const int nx = a.nx, ny = a.ny, N = (int)a.N;
     const float om = a.omega;
     const float w[9] = {a.w0, a.w1, a.w1, a.w1, a.w1, a.w2, a.w2, a.w2, a.w2};
-    // dJ/dG1, dJ/dG2: FP32 per thread over up to 16 sites, then FP64 (only when
-    // a thread has more than 16 sites)
-    double g1 = 0.0, g2 = 0.0;
-    float f1 = 0.f, f2 = 0.f;
-    int nf = 0;
-    bool flushed = false;
+    // dJ/dG1, dJ/dG2: per thread a compensated FP32 sum (Kahan: the running sum
+    // stays within about one FP32 rounding of the exact sum of its terms, however
+    // many sites the thread visits), then accumulate_grid2
+    float f1 = 0.f, f2 = 0.f, c1 = 0.f, c2 = 0.f;
     for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
         const int y = s / nx, x = s % nx;
         float f[9];
@@ -277,19 +299,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
         A.dpsidrho[s] = dpr;
         A.Qx[s] = pc * Fbx;
         A.Qy[s] = pc * Fby;
-        f1 = fmaf(-pc, Fbx * Swx + Fby * Swy, f1);
-        f2 = fmaf(-pc, Fbx * Spx + Fby * Spy, f2);
-        if (++nf == 16) {
-            g1 += f1;
-            g2 += f2;
-            f1 = f2 = 0.f;
-            nf = 0;
-            flushed = true;
-        }
-    }
-    if (flushed) {
-        f1 = (float)(g1 + f1);
-        f2 = (float)(g2 + f2);
+        kahan_add(f1, c1, -pc * (Fbx * Swx + Fby * Swy));
+        kahan_add(f2, c2, -pc * (Fbx * Spx + Fby * Spy));
     }
     accumulate_grid2<kAdjThreads>(f1, f2, A);
 }
@@ -387,19 +398,28 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
     const size_t slot = GE + (size_t)N;                   // populations (GE) then dpsi (N), floats
     cudaStream_t st = s->stream;
 
-    // ---- working memory of one call (freed on return)
+    // ---- working memory of one call (freed on return): checkpoints, two segment
+    // buffers (states 1 .. C-1 of a segment; state 0 is its checkpoint), the
+    // adjoint ping-pong, per-site scratch, and a second stream with its events
     float *ck = nullptr, *seg = nullptr, *lam = nullptr, *scr = nullptr;
     double *tgt = nullptr, *acc = nullptr, *part = nullptr, *grad_dev = nullptr;
     unsigned int* cnt = nullptr;
+    cudaStream_t rs = nullptr;                       // recomputation stream
+    cudaEvent_t ev_fwd = nullptr, ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     auto release = [&]() {
         void* ptrs[] = {ck, seg, lam, scr, tgt, acc, part, grad_dev, cnt};
         for (void* q : ptrs)
             if (q) cudaFree(q);
+        cudaEvent_t evs[] = {ev_fwd, ev_ready[0], ev_ready[1], ev_free[0], ev_free[1]};
+        for (cudaEvent_t e : evs)
+            if (e) cudaEventDestroy(e);
+        if (rs) cudaStreamDestroy(rs);
         cudaGetLastError();
     };
+    const size_t seg_slots = (size_t)(C > 1 ? C - 1 : 1);
     const bool grad_on_dev = dev_ptr(grad_rho);
     bool ok = cudaMalloc((void**)&ck, sizeof(float) * slot * (size_t)(K > 0 ? K : 1)) == cudaSuccess &&
-              cudaMalloc((void**)&seg, sizeof(float) * slot * (size_t)C) == cudaSuccess &&
+              cudaMalloc((void**)&seg, sizeof(float) * slot * 2 * seg_slots) == cudaSuccess &&
               cudaMalloc((void**)&lam, sizeof(float) * 18 * (size_t)N) == cudaSuccess &&
               cudaMalloc((void**)&scr, sizeof(float) * 6 * (size_t)N) == cudaSuccess &&
               cudaMalloc((void**)&tgt, sizeof(double) * N) == cudaSuccess &&
@@ -410,6 +430,15 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
     if (!ok) {
         release();
         return LB_ERR_OOM;
+    }
+    if (cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_fwd, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_ready[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_ready[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_free[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_free[1], cudaEventDisableTiming) != cudaSuccess) {
+        release();
+        return LB_ERR_CUDA;
     }
     auto fail = [&]() {
         release();
@@ -468,27 +497,43 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
     k_adj_terminal<float><<<grid, kAdjThreads, 0, st>>>(A, A.g);
     if (cudaGetLastError() != cudaSuccess) return fail();
 
-    // ---- reverse over the segments, recomputing each from its checkpoint
+    // ---- reverse over the segments. Segment k (states kC .. kC + n - 1) is
+    // recomputed from its checkpoint into segment buffer k & 1 on the second
+    // stream while the reverse sweep of segment k + 1 runs on the caller's
+    // stream (both are latency-bound on lattices that fit in L2, so the two
+    // overlap); events order the buffer reuse and the hand-over.
     A.acc = acc + 4;         // acc[4], acc[5] = the steps' dJ/dG1, dJ/dG2
     const StepArgs<float> base = state_args<float>(s, 0);
-    for (long long k = K - 1; k >= 0; --k) {
-        const long long t0 = k * C;
-        const long long n = (k + 1) * C <= T ? C : T - t0;
-        if (cudaMemcpyAsync(seg, ck + slot * k, sizeof(float) * slot, cudaMemcpyDeviceToDevice,
-                            st) != cudaSuccess)
-            return fail();
-        for (long long j = 0; j + 1 < n; ++j) {
+    auto seg_len = [&](long long k) { return (k + 1) * C <= T ? C : T - k * C; };
+    auto state_at = [&](long long k, long long j) -> float* {
+        return j == 0 ? ck + slot * k : seg + slot * ((size_t)(k & 1) * seg_slots + (j - 1));
+    };
+    bool used[2] = {false, false};
+    auto recompute = [&](long long k) -> bool {
+        const int b = (int)(k & 1);
+        if (used[b] && cudaStreamWaitEvent(rs, ev_free[b], 0) != cudaSuccess) return false;
+        used[b] = true;
+        for (long long j = 0; j + 1 < seg_len(k); ++j) {
             StepArgs<float> a = base;
-            float* in = seg + slot * j;
-            float* out = seg + slot * (j + 1);
+            const float* in = state_at(k, j);
+            float* out = state_at(k, j + 1);
             a.g_in = in;
             a.g_out = out;
             a.dpsi_in = in + GE;
             a.dpsi_out = out + GE;
-            if (fp32_step(a, L, false, st) != cudaSuccess) return fail();
+            if (fp32_step(a, L, false, rs) != cudaSuccess) return false;
         }
+        return cudaEventRecord(ev_ready[b], rs) == cudaSuccess;
+    };
+    if (cudaEventRecord(ev_fwd, st) != cudaSuccess || cudaStreamWaitEvent(rs, ev_fwd, 0) != cudaSuccess)
+        return fail();
+    if (K > 0 && !recompute(K - 1)) return fail();
+    for (long long k = K - 1; k >= 0; --k) {
+        const long long n = seg_len(k);
+        if (k > 0 && !recompute(k - 1)) return fail();
+        if (cudaStreamWaitEvent(st, ev_ready[k & 1], 0) != cudaSuccess) return fail();
         for (long long j = n - 1; j >= 0; --j) {
-            const float* state = seg + slot * j;
+            const float* state = state_at(k, j);
             A.g = state;
             A.dpsi = state + GE;
             A.lam_next = lamA;
@@ -500,6 +545,7 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
             lamA = lamB;
             lamB = tmp;
         }
+        if (cudaEventRecord(ev_free[k & 1], st) != cudaSuccess) return fail();
     }
     double* gout = grad_on_dev ? grad_rho : grad_dev;
     k_adj_grad_init<<<adj_grid(N), kAdjThreads, 0, st>>>(lamA, N, A.a.w0, A.a.w1, A.a.w2, gout);

@@ -32,9 +32,10 @@
 //      rho(t+1); the row behind r is then complete and its dpsi(t+1) is written.
 // One __syncthreads per row orders the exchange and the ring updates.
 // REDUCE launches also accumulate mass and the Sec. 5 pseudo-energies of
-// state t (FP32 per thread for 64 rows, then FP64), reduce them per CTA in
-// FP64 and let the last CTA to finish sum all CTA partials in a fixed order
-// into one trace row — deterministic for a given launch shape.
+// state t (evaluated from the same stencil values as the force; FP32 per
+// thread for 64 rows, then FP64), reduce them per CTA in FP64 and let the last
+// CTA to finish sum all CTA partials in a fixed order into one trace row —
+// deterministic for a given launch shape.
 #include "lb_device.cuh"
 
 #include <cmath>
@@ -75,7 +76,7 @@ __device__ __forceinline__ int step_row(int off, int stride, int total)
 template <typename T, int BX, bool REDUCE, bool OM1, int DIR>
 __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int by, double v[4],
                                               float (*win)[BX + 4], float4 (*exR)[BX + 2],
-                                              float4 (*exL)[BX + 2])
+                                              float4 (*exL)[BX + 2], double* eacc)
 {
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
@@ -114,8 +115,14 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     // (G+ + G0) + G- whatever the direction: hb = ahead-group sum of the behind
     // row, zb = zero-group sum of the behind row, hc = ahead-group sum of row r.
     float hb = 0.f, zb = 0.f, hc = 0.f;
+    // energy/mass sums: FP32 in registers for up to 64 rows, then flushed into
+    // this thread's FP64 slots in shared memory (eacc[q * BX + tid]), which keeps
+    // the FP64 accumulators out of the registers of the row loop
     float es = 0.f, em = 0.f, eb = 0.f, ms = 0.f;
-    double d_es = 0.0, d_em = 0.0, d_eb = 0.0, d_ms = 0.0;
+    if (REDUCE) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) eacc[q * BX + tid] = 0.0;
+    }
 
     for (int k = 0; k <= nrows + 1; ++k) {
         const int r = r0 + DIR * k;
@@ -136,12 +143,12 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
 #pragma unroll
         for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
         const float pc = a.psi_ref + rows[2][0];
+        const bool out_site = out_col && r >= y0 && r < y1;
         float Sx, Sy;
-        force_sums(rows, a, Sx, Sy);
+        // the force, and on reduction steps the Sec. 5 energies of state t at (x, r)
+        force_energy<REDUCE>(rows, a, Sx, Sy, out_site, pc, es, em, eb);
         float gs[9];
         const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
-
-        const bool out_site = out_col && r >= y0 && r < y1;
         if (REDUCE && out_site) ms += d;
 
         // ---- exchange post-collision values with the neighbouring columns
@@ -201,21 +208,21 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fn[i];
         if (REDUCE && out_site) {
-            // Sec. 5 energies of state t at (x, r); the dpsi rows r-2..r+2 stay in the
-            // ring until the next iteration overwrites slot (r + 4 DIR) & 7
-            energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
             if ((k & 63) == 63) {
-                d_es += es; d_em += em; d_eb += eb; d_ms += ms;
+                eacc[0 * BX + tid] += es;
+                eacc[1 * BX + tid] += em;
+                eacc[2 * BX + tid] += eb;
+                eacc[3 * BX + tid] += ms;
                 es = em = eb = ms = 0.f;
             }
         }
     }
 
     if (REDUCE) {
-        v[0] = d_es + es;
-        v[1] = d_em + em;
-        v[2] = d_eb + eb;
-        v[3] = d_ms + ms;
+        v[0] = eacc[0 * BX + tid] + es;
+        v[1] = eacc[1 * BX + tid] + em;
+        v[2] = eacc[2 * BX + tid] + eb;
+        v[3] = eacc[3 * BX + tid] + ms;
     }
 }
 
@@ -232,10 +239,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
     __shared__ float win[8][BX + 4];          // dpsi(t) rows, slot = row & 7
     __shared__ float4 exR[2][BX + 2];        // right-moving f*: speeds 8, 1, 5 (cy = -1, 0, +1)
     __shared__ float4 exL[2][BX + 2];        // left-moving f*: speeds 7, 3, 6
+    __shared__ double eacc[REDUCE ? 4 * BX : 1];   // FP64 energy/mass slots of the threads
     if (ALTERNATE && !REDUCE && alternate && (by & 1))
-        step_tile_dir<T, BX, REDUCE, OM1, -1>(a, bx, by, v, win, exR, exL);
+        step_tile_dir<T, BX, REDUCE, OM1, -1>(a, bx, by, v, win, exR, exL, eacc);
     else
-        step_tile_dir<T, BX, REDUCE, OM1, +1>(a, bx, by, v, win, exR, exL);
+        step_tile_dir<T, BX, REDUCE, OM1, +1>(a, bx, by, v, win, exR, exL, eacc);
 }
 
 template <typename T, int BX, bool REDUCE, bool OM1>
@@ -264,7 +272,7 @@ __global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / B
 // replica's partials in the order k_step's last CTA uses, so a replica's
 // fields and trace are bit-identical to running it alone with the same shape.
 template <typename T, int BX, bool REDUCE, bool OM1>
-__global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
+__global__ void __launch_bounds__(BX, (REDUCE ? 24 : 40) * 32 / BX)
     k_step_batch(const StepArgs<T>* __restrict__ args, const int4* __restrict__ tiles, int ntiles,
                  double* __restrict__ tile_partials)
 {
