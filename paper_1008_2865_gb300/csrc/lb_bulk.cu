@@ -235,13 +235,14 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
 #pragma unroll
         for (int k = 0; k < 5; ++k) rows[k] = pring + ((it + k) % NP) * WP + ppos;
         const float pc = a.psi_ref + rows[2][0];
-        const bool out_site = out_col && r >= y0 && r < y1;
         float Sx, Sy;
-        // the force, and on reduction steps the Sec. 5 energies of state t at (x, r)
-        force_energy<REDUCE>(rows, a, Sx, Sy, out_site, pc, es, em, eb);
+        force_sums(rows, a, Sx, Sy);
         float gs[9];
         const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
+
+        const bool out_site = out_col && r >= y0 && r < y1;
         if (REDUCE && out_site) {
+            energy_site(rows, pc, a, es, em, eb);
             ms += d;
             if (((r - y0) & 63) == 63) {
                 d_es += es; d_em += em; d_eb += eb; d_ms += ms;

@@ -32,10 +32,9 @@
 //      rho(t+1); the row behind r is then complete and its dpsi(t+1) is written.
 // One __syncthreads per row orders the exchange and the ring updates.
 // REDUCE launches also accumulate mass and the Sec. 5 pseudo-energies of
-// state t (evaluated from the same stencil values as the force; FP32 per
-// thread for 64 rows, then FP64), reduce them per CTA in FP64 and let the last
-// CTA to finish sum all CTA partials in a fixed order into one trace row —
-// deterministic for a given launch shape.
+// state t (FP32 per thread for 64 rows, then FP64), reduce them per CTA in
+// FP64 and let the last CTA to finish sum all CTA partials in a fixed order
+// into one trace row — deterministic for a given launch shape.
 #include "lb_device.cuh"
 
 #include <cmath>
@@ -76,7 +75,7 @@ __device__ __forceinline__ int step_row(int off, int stride, int total)
 template <typename T, int BX, bool REDUCE, bool OM1, int DIR>
 __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int by, double v[4],
                                               float (*win)[BX + 4], float4 (*exR)[BX + 2],
-                                              float4 (*exL)[BX + 2], double* eacc)
+                                              float4 (*exL)[BX + 2])
 {
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
@@ -115,14 +114,8 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     // (G+ + G0) + G- whatever the direction: hb = ahead-group sum of the behind
     // row, zb = zero-group sum of the behind row, hc = ahead-group sum of row r.
     float hb = 0.f, zb = 0.f, hc = 0.f;
-    // energy/mass sums: FP32 in registers for up to 64 rows, then flushed into
-    // this thread's FP64 slots in shared memory (eacc[q * BX + tid]), which keeps
-    // the FP64 accumulators out of the registers of the row loop
     float es = 0.f, em = 0.f, eb = 0.f, ms = 0.f;
-    if (REDUCE) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) eacc[q * BX + tid] = 0.0;
-    }
+    double d_es = 0.0, d_em = 0.0, d_eb = 0.0, d_ms = 0.0;
 
     for (int k = 0; k <= nrows + 1; ++k) {
         const int r = r0 + DIR * k;
@@ -143,12 +136,12 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
 #pragma unroll
         for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
         const float pc = a.psi_ref + rows[2][0];
-        const bool out_site = out_col && r >= y0 && r < y1;
         float Sx, Sy;
-        // the force, and on reduction steps the Sec. 5 energies of state t at (x, r)
-        force_energy<REDUCE>(rows, a, Sx, Sy, out_site, pc, es, em, eb);
+        force_sums(rows, a, Sx, Sy);
         float gs[9];
         const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
+
+        const bool out_site = out_col && r >= y0 && r < y1;
         if (REDUCE && out_site) ms += d;
 
         // ---- exchange post-collision values with the neighbouring columns
@@ -208,21 +201,21 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fn[i];
         if (REDUCE && out_site) {
+            // Sec. 5 energies of state t at (x, r); the dpsi rows r-2..r+2 stay in the
+            // ring until the next iteration overwrites slot (r + 4 DIR) & 7
+            energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
             if ((k & 63) == 63) {
-                eacc[0 * BX + tid] += es;
-                eacc[1 * BX + tid] += em;
-                eacc[2 * BX + tid] += eb;
-                eacc[3 * BX + tid] += ms;
+                d_es += es; d_em += em; d_eb += eb; d_ms += ms;
                 es = em = eb = ms = 0.f;
             }
         }
     }
 
     if (REDUCE) {
-        v[0] = eacc[0 * BX + tid] + es;
-        v[1] = eacc[1 * BX + tid] + em;
-        v[2] = eacc[2 * BX + tid] + eb;
-        v[3] = eacc[3 * BX + tid] + ms;
+        v[0] = d_es + es;
+        v[1] = d_em + em;
+        v[2] = d_eb + eb;
+        v[3] = d_ms + ms;
     }
 }
 
@@ -239,11 +232,10 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
     __shared__ float win[8][BX + 4];          // dpsi(t) rows, slot = row & 7
     __shared__ float4 exR[2][BX + 2];        // right-moving f*: speeds 8, 1, 5 (cy = -1, 0, +1)
     __shared__ float4 exL[2][BX + 2];        // left-moving f*: speeds 7, 3, 6
-    __shared__ double eacc[REDUCE ? 4 * BX : 1];   // FP64 energy/mass slots of the threads
     if (ALTERNATE && !REDUCE && alternate && (by & 1))
-        step_tile_dir<T, BX, REDUCE, OM1, -1>(a, bx, by, v, win, exR, exL, eacc);
+        step_tile_dir<T, BX, REDUCE, OM1, -1>(a, bx, by, v, win, exR, exL);
     else
-        step_tile_dir<T, BX, REDUCE, OM1, +1>(a, bx, by, v, win, exR, exL, eacc);
+        step_tile_dir<T, BX, REDUCE, OM1, +1>(a, bx, by, v, win, exR, exL);
 }
 
 template <typename T, int BX, bool REDUCE, bool OM1>
@@ -264,32 +256,54 @@ __global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / B
 
 // ---------------------------------------------------------------- batches
 // Several lattices (replicas, each with its own size and couplings) advanced by
-// one launch: a persistent grid strides over a work list of tiles, each tile
-// = (replica, strip, row chunk) of that replica's own launch shape, and runs
-// exactly the per-tile code of k_step. The replica's arguments are staged in
-// shared memory once per tile. With REDUCE each tile's CTA partial (the same
-// block sum k_step forms) goes to tile_partials; k_batch_reduce then sums a
-// replica's partials in the order k_step's last CTA uses, so a replica's
-// fields and trace are bit-identical to running it alone with the same shape.
-template <typename T, int BX, bool REDUCE, bool OM1>
-__global__ void __launch_bounds__(BX, (REDUCE ? 24 : 40) * 32 / BX)
+// one launch: a persistent grid takes tiles from a work list, each tile =
+// (replica, strip, row chunk) of that replica's own launch shape, and runs
+// exactly the per-tile code of k_step. Tiles are handed out by an atomic
+// counter (sched[0]), so a CTA that finishes early takes the next tile
+// instead of waiting for a fixed share; the last CTA to leave resets the
+// counters (sched[1] counts the CTAs that left) for the next launch. The
+// replica's arguments are staged in shared memory once per tile. Plain steps
+// march in alternating directions per row chunk when `alternate` is set (the
+// fields do not depend on the direction); reduction steps march down. With
+// REDUCE each tile's CTA partial (the same block sum k_step forms) goes to
+// tile_partials; k_batch_reduce then sums a replica's partials in the order
+// k_step's last CTA uses, so a replica's fields and trace are bit-identical to
+// running it alone with the same shape.
+template <typename T, int BX, bool REDUCE, bool OM1, bool ALT>
+__global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
     k_step_batch(const StepArgs<T>* __restrict__ args, const int4* __restrict__ tiles, int ntiles,
-                 double* __restrict__ tile_partials)
+                 double* __restrict__ tile_partials, unsigned int* __restrict__ sched)
 {
     __shared__ StepArgs<T> sa;
-    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
-        const int4 tl = tiles[k];                   // (replica, strip, chunk, -)
-        __syncthreads();                            // previous tile done with sa and smem rings
-        if (threadIdx.x == 0) sa = args[tl.x];
+    __shared__ int s_k;
+    for (;;) {
+        __syncthreads();                            // previous tile done with sa, s_k and the rings
+        if (threadIdx.x == 0) {
+            const int k = (int)atomicAdd(&sched[0], 1u);
+            s_k = k;
+            if (k < ntiles) sa = args[tiles[k].x];
+        }
         __syncthreads();
+        const int k = s_k;
+        if (k >= ntiles) break;
+        const int4 tl = tiles[k];                   // (replica, strip, chunk, -)
         double v[4];
-        step_tile<T, BX, REDUCE, OM1, false>(sa, tl.y, tl.z, v);
+        step_tile<T, BX, REDUCE, OM1, ALT>(sa, tl.y, tl.z, v);
         if (REDUCE) {
             block_sum4<BX>(v);
             if (threadIdx.x == 0) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) tile_partials[4 * (size_t)k + q] = v[q];
             }
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&sched[1], 1u) == gridDim.x - 1) {
+            // every CTA has taken its last tile number: reset for the next launch
+            sched[0] = 0u;
+            sched[1] = 0u;
+            __threadfence();
         }
     }
 }
@@ -482,14 +496,20 @@ cudaError_t launch_batch_bx(const BatchLaunch<T>& b, bool reduce, cudaStream_t s
         long long grid = (long long)per_sm * b.num_sms;
         if (grid > b.ntiles) grid = b.ntiles;
         if (grid < 1) grid = 1;
-        kern<<<(unsigned int)grid, BX, 0, s>>>(b.args, b.tiles, b.ntiles, b.tile_partials);
+        kern<<<(unsigned int)grid, BX, 0, s>>>(b.args, b.tiles, b.ntiles, b.tile_partials,
+                                               b.sched);
         return cudaGetLastError();
     };
     cudaError_t e;
     if (reduce)
-        e = b.om1 ? pick(k_step_batch<T, BX, true, true>) : pick(k_step_batch<T, BX, true, false>);
+        e = b.om1 ? pick(k_step_batch<T, BX, true, true, false>)
+                  : pick(k_step_batch<T, BX, true, false, false>);
+    else if (b.alternate)
+        e = b.om1 ? pick(k_step_batch<T, BX, false, true, true>)
+                  : pick(k_step_batch<T, BX, false, false, true>);
     else
-        e = b.om1 ? pick(k_step_batch<T, BX, false, true>) : pick(k_step_batch<T, BX, false, false>);
+        e = b.om1 ? pick(k_step_batch<T, BX, false, true, false>)
+                  : pick(k_step_batch<T, BX, false, false, false>);
     if (e != cudaSuccess || !reduce) return e;
     k_batch_reduce<BX><<<b.nreps, BX, 0, s>>>(b.tile_partials, b.reps, b.trace_every);
     return cudaGetLastError();

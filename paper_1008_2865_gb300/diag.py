@@ -15,6 +15,21 @@
 - thermal_energy(rho): E_th = rho_mean cs^2 L^2 (Sec. 5, Fig. 5).
 - summary(rho, energies): the above plus E/E_th, E_m/E_s and the surface share
   (E - E_bulk) / |E_bulk| of the pseudo-energy (Sec. 5, Figs. 5 and 7).
+- energy_series(trace, n_sites): the time series of Figs. 5 and 7 from the
+  library's trace rows (t, mass, E_s, E_m, E_bulk): E/E_th, E_m/E_s and the
+  surface share, with E_th = rho_mean cs^2 N and rho_mean = mass / N.
+- growth_exponent(t, R, t0): the exponent alpha of R(t) ~ (t - t0)^alpha
+  (Sec. 4: 1/3 for diffusive growth, 1/6 and 1/5 for the slowed cases) by a
+  least-squares fit of log R against log(t - t0).
+- surface_energy(rho, G1, G2): E_surf of Sec. 5 (Eq. Esurf) in weak-gradient
+  form, c sum_x |grad psi|^2 with central differences on the periodic lattice;
+  c = -A1/12 (the second-order expansion of the Sec. 5 sums under the
+  normalisations of Eqs. weights_1 and weights_2, A1 = G1 + G2) by default,
+  or c = A2/2 as printed (A2 = G1 + 3/2 G2) with coefficient="printed".
+- surface_tension(psi_profile, G1, G2): gamma of Eq. gamma per interface,
+  -(G1 + 12/7 G2)/2 cs^4 integral |d psi/dy|^2 dy, on a periodic profile across
+  a flat slab (two interfaces; the integral is halved), central differences,
+  unit lattice spacing.
 
 Densities are NumPy arrays [ny, nx] (row-major [y][x]); nothing here is on the
 GPU path. The FFT is NumPy's.
@@ -139,3 +154,61 @@ def summary(rho, energies=None):
         out.update({"E_over_Eth": E / thermal_energy(rho), "Em_over_Es": em / es,
                     "E_surface_share": (E - eb) / abs(eb) if eb != 0 else 0.0})
     return out
+
+
+def psi_of(rho, rho0: float = 1.0):
+    """psi = sqrt(rho0) (1 - exp(-rho / rho0)) (Sec. 2)."""
+    return math.sqrt(rho0) * -np.expm1(-np.asarray(rho, dtype=np.float64) / rho0)
+
+
+def energy_series(trace, n_sites: int):
+    """Figs. 5 and 7 from trace rows (t, mass, E_s, E_m, E_bulk): a dict of arrays
+    t, E_over_Eth, Em_over_Es, surface_share ((E - E_bulk) / |E_bulk|)."""
+    tr = np.asarray(trace, dtype=np.float64).reshape(-1, 5)
+    t, mass, es, em, eb = (tr[:, k] for k in range(5))
+    e = es + em
+    eth = (mass / n_sites) * CS2 * n_sites
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return {"t": t, "E_over_Eth": e / eth, "Em_over_Es": em / es,
+                "surface_share": (e - eb) / np.abs(eb)}
+
+
+def growth_exponent(t, R, t0: float = 0.0):
+    """alpha of R(t) ~ (t - t0)^alpha: least-squares slope of log R on log(t - t0)."""
+    t = np.asarray(t, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    sel = (t > t0) & np.isfinite(R) & (R > 0)
+    if np.count_nonzero(sel) < 2:
+        return float("nan")
+    x = np.log(t[sel] - t0)
+    y = np.log(R[sel])
+    return float(np.polyfit(x, y, 1)[0])
+
+
+def _grad_sq(psi):
+    """|grad psi|^2 by central differences on the periodic lattice."""
+    gx = 0.5 * (np.roll(psi, -1, axis=1) - np.roll(psi, 1, axis=1))
+    gy = 0.5 * (np.roll(psi, -1, axis=0) - np.roll(psi, 1, axis=0))
+    return gx * gx + gy * gy
+
+
+def surface_energy(rho, G1: float, G2: float, rho0: float = 1.0, coefficient: str = "expansion",
+                   lam: float = 1.5):
+    """E_surf = c sum_x |grad psi|^2 (Eq. Esurf), c = -A1/12 ("expansion") or A2/2
+    ("printed", A2 = G1 + lam G2)."""
+    psi = psi_of(rho, rho0)
+    if coefficient == "expansion":
+        c = -(G1 + G2) / 12.0
+    elif coefficient == "printed":
+        c = (G1 + lam * G2) / 2.0
+    else:
+        raise ValueError(f"unknown coefficient {coefficient!r}")
+    return float(c * _grad_sq(psi).sum())
+
+
+def surface_tension(psi_profile, G1: float, G2: float, interfaces: int = 2):
+    """gamma of Eq. gamma for each of the `interfaces` interfaces of a periodic
+    profile psi(y) across a flat slab: -(G1 + 12/7 G2)/2 cs^4 sum_y (d psi/dy)^2 / interfaces."""
+    p = np.asarray(psi_profile, dtype=np.float64)
+    d = 0.5 * (np.roll(p, -1) - np.roll(p, 1))
+    return float(-(G1 + 12.0 / 7.0 * G2) / 2.0 * CS2 * CS2 * np.sum(d * d) / interfaces)

@@ -60,3 +60,57 @@ def test_thermal_energy_and_summary():
     s = diag.summary(rho + 0.001 * np.cos(np.arange(10))[None, :], energies=(-2.0, -0.1, -2.2, 60.0))
     assert s["droplets"] == 0 and math.isclose(s["Em_over_Es"], 0.05)
     assert math.isclose(s["E_surface_share"], 0.1 / 2.2)
+
+
+def test_energy_series_of_a_trace():
+    """Figs. 5 and 7 series from trace rows: E/E_th with E_th = (mass/N) cs^2 N,
+    E_m/E_s and the surface share (E - E_bulk)/|E_bulk|."""
+    tr = np.array([[0.0, 70.0, -20.0, 1.0, -21.0],
+                   [10.0, 70.0, -30.0, 2.0, -29.0]])
+    s = diag.energy_series(tr, 100)
+    assert list(s["t"]) == [0.0, 10.0]
+    assert np.allclose(s["E_over_Eth"], [-19.0 / (0.7 / 3 * 100), -28.0 / (0.7 / 3 * 100)])
+    assert np.allclose(s["Em_over_Es"], [-0.05, -2.0 / 30.0])
+    assert np.allclose(s["surface_share"], [2.0 / 21.0, 1.0 / 29.0])
+
+
+def test_growth_exponent_of_power_laws():
+    t = np.array([1e3, 2e3, 5e3, 1e4, 5e4, 1e5])
+    for alpha, t0 in ((1 / 3, 0.0), (1 / 6, 200.0), (0.2, 50.0)):
+        R = 3.0 * (t - t0) ** alpha
+        assert math.isclose(diag.growth_exponent(t, R, t0), alpha, rel_tol=1e-12)
+    assert math.isclose(diag.growth_exponent(t, np.full_like(t, 7.0)), 0.0, abs_tol=1e-12)
+
+
+def test_surface_tension_of_a_tanh_profile():
+    """Eq. gamma on psi = a + (b/2)(tanh((y-y1)/w) - tanh((y-y2)/w)): per interface
+    the integral of (psi')^2 is (b/2)^2 4/(3w), so gamma = -(G1 + 12/7 G2)/2 cs^4
+    b^2/(3w); central differences are within (pi/w)^2-order of it."""
+    w, b = 20.0, 0.3
+    y = np.arange(400)
+    p = 0.5 + 0.5 * b * (np.tanh((y - 100) / w) - np.tanh((y - 300) / w))
+    for G1, G2 in ((-5.0, 0.0), (-13.1, 8.2)):
+        exact = -(G1 + 12.0 / 7.0 * G2) / 2.0 / 9.0 * b * b / (3.0 * w)
+        assert math.isclose(diag.surface_tension(p, G1, G2), exact, rel_tol=2e-3)
+
+
+def test_surface_energy_against_the_lattice_sums():
+    """E_surf = -(A1/12) sum |grad psi|^2 is the weak-gradient limit of E - E_bulk of the
+    Sec. 5 lattice sums (computed here by the oracle): on a smooth field the relative
+    gap shrinks as k^2 (m = 1, 2: 6e-4, 2.4e-3). The printed A2/2 coefficient has the
+    opposite sign for A2 < 0 and does not match."""
+    import oracle
+    L = 128
+    x = np.arange(L)[None, :].repeat(L, 0)
+    gaps = []
+    for m in (1, 2):
+        rho = 0.7 + 0.05 * np.cos(2 * math.pi * m * x / L) + 0.03 * np.sin(2 * math.pi * m * x.T / L)
+        psi = diag.psi_of(rho)
+        for G1, G2 in ((-5.0, 0.0), (-5.0, 0.6)):
+            es, em, eb = oracle.energy(psi, G1, G2)
+            exact = es + em - eb
+            gap = abs(diag.surface_energy(rho, G1, G2) / exact - 1.0)
+            gaps.append(gap)
+            assert gap <= (1e-3 if m == 1 else 4e-3)
+            assert diag.surface_energy(rho, G1, G2, coefficient="printed") * exact < 0
+    assert 3.0 < gaps[2] / gaps[0] < 5.0          # k^2 scaling between m = 1 and m = 2
