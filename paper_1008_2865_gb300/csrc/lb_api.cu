@@ -347,44 +347,29 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
         free_state(s);
         return LB_ERR_OOM;
     }
-    // rho_init where the kernels can read it: in place (device memory, or pinned
-    // host memory read over the host link), else copied into a temporary
-    double* rho_dev = nullptr;   // a temporary, not one of the state's guarded buffers
-    const double* rho_in = device_view(const_cast<double*>(rho_init));
-    if (!rho_in) {
-        if (cudaMalloc((void**)&rho_dev, sizeof(double) * N) != cudaSuccess) {
-            cudaGetLastError();
-            free_state(s);
-            return LB_ERR_OOM;
-        }
-        rho_in = rho_dev;
-    }
+    // rho_init is copied once (one DMA transfer, whatever memory it is in) into the
+    // second population buffer, which holds nothing until the first step writes it
+    // and is at least 8 N bytes in every precision; the checks and the
+    // initialisation then read device memory only.
+    double* rho_in = static_cast<double*>(p->prec == LB_FP64 ? (void*)s->f64[1] : s->g[1]);
     auto bail = [&](lb_status st) {
-        if (rho_dev) cudaFree(rho_dev);
         cudaGetLastError();
         free_state(s);
         return st;
     };
-    if ((rho_dev && cudaMemcpyAsync(rho_dev, rho_init, sizeof(double) * N, cudaMemcpyHostToDevice,
-                                    s->stream) != cudaSuccess) ||
+    if (cudaMemcpyAsync(rho_in, rho_init, sizeof(double) * N, cudaMemcpyDefault, s->stream) !=
+            cudaSuccess ||
         cudaMemsetAsync(s->counter, 0, sizeof(unsigned int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->trace_count, 0, sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->flag, 0, sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->err, 0, sizeof(int), s->stream) != cudaSuccess)
         return bail(LB_ERR_CUDA);
-    if (p->prec != LB_FP64 && g_pitch(p->nx) != 9 * p->nx) {
-        // the padding columns of the tiled populations hold zeros in both buffers
-        // (nx not a multiple of 32; otherwise every element is written by the init)
-        const size_t gb = elem_size(p->prec) * (size_t)g_elems(p->nx, p->ny);
-        if (cudaMemsetAsync(s->g[0], 0, gb, s->stream) != cudaSuccess ||
-            cudaMemsetAsync(s->g[1], 0, gb, s->stream) != cudaSuccess)
-            return bail(LB_ERR_CUDA);
-    }
     if (rho_check_sum(rho_in, N, s->partials, s->counter, s->res, s->flag, s->stream) !=
         cudaSuccess)
         return bail(LB_ERR_CUDA);
     double sum = 0.0;
     int flag = 0;
+    // after this synchronisation the caller's rho_init is no longer read
     if (cudaMemcpyAsync(&sum, s->res, sizeof(double), cudaMemcpyDeviceToHost, s->stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(&flag, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream) !=
@@ -396,6 +381,10 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
     // the deviations at init and the mass/field reconstructions use it in FP64,
     // and all of them must mean the same number.
     s->rho_ref = (double)(float)(p->rho_ref > 0.0 ? p->rho_ref : sum / (double)N);
+    const bool padded = p->prec != LB_FP64 && g_pitch(p->nx) != 9 * p->nx;
+    const size_t gbytes = elem_size(p->prec) * (size_t)g_elems(p->nx, p->ny);
+    if (padded && cudaMemsetAsync(s->g[0], 0, gbytes, s->stream) != cudaSuccess)
+        return bail(LB_ERR_CUDA);
     cudaError_t e;
     if (p->prec == LB_FP64)
         e = fp64_init(s->f64[0], rho_in, p->nx, p->ny, s->stream);
@@ -405,9 +394,13 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
     else
         e = delta_init<__half>(static_cast<__half*>(s->g[0]), s->dpsi[0], rho_in, p->nx, p->ny,
                                s->rho_ref, p->rho0, s->stream);
-    if (e != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess)
+    if (e != cudaSuccess) return bail(LB_ERR_CUDA);
+    // the padding columns of the tiled populations hold zeros in both buffers (nx
+    // not a multiple of 32; otherwise every element of g[0] is written by the
+    // initialisation and every element of g[1] by the first step); g[1] is
+    // cleared after the initialisation has read rho_init from it
+    if (padded && cudaMemsetAsync(s->g[1], 0, gbytes, s->stream) != cudaSuccess)
         return bail(LB_ERR_CUDA);
-    if (rho_dev) cudaFree(rho_dev);
     *out = s;
     return LB_OK;
 }

@@ -32,7 +32,6 @@ struct lb_batch {
     double* d_partials = nullptr;
     BatchRep* d_reps = nullptr;
     unsigned int* d_sched = nullptr;        // tile scheduler counters of k_step_batch
-    bool alternate = false;                 // plain steps alternate the march (state > L2)
     // graph of one period of steps, starting at t % period == 0
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -80,10 +79,8 @@ lb_status build_tables(lb_batch* b)
     free_tables(b);
     std::vector<int4> tiles;
     std::vector<BatchRep> info;
-    long long state_bytes = 0;
     for (size_t r = 0; r < b->reps.size(); ++r) {
         const lb_state* s = b->reps[r];
-        state_bytes += s->N * (long long)(2 * (9 * elem_size(s->p.prec) + 4));
         const int ntx = (s->p.nx + b->block_x - 3) / (b->block_x - 2);
         const int nty = (s->p.ny + b->rows - 1) / b->rows;
         BatchRep ri;
@@ -99,9 +96,6 @@ lb_status build_tables(lb_batch* b)
             for (int bx = 0; bx < ntx; ++bx) tiles.push_back(make_int4((int)r, bx, by, 0));
     }
     b->ntiles = (int)tiles.size();
-    // Alternating march directions pay when the batch's state does not fit in L2
-    // (the halo rows of a chunk boundary are then re-read from HBM).
-    b->alternate = state_bytes > (128LL << 20);
     const bool ok =
         (b->prec == LB_FP32 ? upload_args<float>(b) : upload_args<__half>(b)) &&
         cudaMalloc((void**)&b->d_tiles, sizeof(int4) * tiles.size()) == cudaSuccess &&
@@ -128,14 +122,12 @@ cudaError_t enqueue_step(const lb_batch* b, cudaStream_t s, long long t, int cur
     if (b->prec == LB_FP32) {
         BatchLaunch<float> L{static_cast<const StepArgs<float>*>(b->d_args[cur]), b->d_tiles,
                              b->ntiles, b->d_partials, b->d_reps, (int)b->reps.size(),
-                             b->block_x, b->om1, b->trace_every, b->num_sms, b->d_sched,
-                             b->alternate};
+                             b->block_x, b->om1, b->trace_every, b->num_sms, b->d_sched};
         return fp32_batch_step(L, reduce, s);
     }
     BatchLaunch<__half> L{static_cast<const StepArgs<__half>*>(b->d_args[cur]), b->d_tiles,
                           b->ntiles, b->d_partials, b->d_reps, (int)b->reps.size(),
-                          b->block_x, b->om1, b->trace_every, b->num_sms, b->d_sched,
-                          b->alternate};
+                          b->block_x, b->om1, b->trace_every, b->num_sms, b->d_sched};
     return fp16_batch_step(L, reduce, s);
 }
 

@@ -87,16 +87,23 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     const int nrows = y1 - y0;
     const int txe = min(BX - 2, nx - x0);
     const bool out_col = tid >= 1 && tid <= txe;
+    // A strip narrower than the CTA (the last strip of a row of tiles) needs the
+    // threads up to txe + 1 (the right halo collision) and, for the dpsi ring,
+    // up to txe + 5; a warp holding none of them skips all work and only keeps
+    // the row barriers (warp-uniform).
+    const bool wact = (tid & ~31) <= txe + 5;
     const int xc = wrapi(x0 - 1 + tid, nx);
     const int pc0 = wrapi(x0 - 3 + tid, nx);
     const int pc1 = wrapi(x0 - 3 + BX + (tid & 3), nx);
     const int cx = tcol(xc);
     const int r0 = DIR > 0 ? y0 - 1 : y1;    // first collision row
 
-    for (int rr = r0 - 2; rr <= r0 + 2; ++rr) {
-        const float* src = a.dpsi_in + wrapi(rr, ny) * nx;
-        win[rr & 7][tid] = __ldg(src + pc0);
-        if (tid < 4) win[rr & 7][BX + tid] = __ldg(src + pc1);
+    if (wact) {
+        for (int rr = r0 - 2; rr <= r0 + 2; ++rr) {
+            const float* src = a.dpsi_in + wrapi(rr, ny) * nx;
+            win[rr & 7][tid] = __ldg(src + pc0);
+            if (tid < 4) win[rr & 7][BX + tid] = __ldg(src + pc1);
+        }
     }
     // Row offsets (row * P) of g, periodic, kept incrementally: at the top of
     // iteration r, sb, sc, sa hold rows r-DIR (behind), r, r+DIR (ahead) and oq
@@ -107,7 +114,7 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     int oq = wrapi(r0 + 3 * DIR, ny) * nx;
 
     float f[9];
-    load_site(f, a.g_in + (sc + cx));
+    if (wact) load_site(f, a.g_in + (sc + cx));
     __syncthreads();
 
     // rho(t+1) of a row from its three speed groups (c_y = +1, 0, -1), summed as
@@ -119,96 +126,105 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
 
     for (int k = 0; k <= nrows + 1; ++k) {
         const int r = r0 + DIR * k;
-        // ---- prefetch: dpsi row r+3 DIR and the populations of row r+DIR
         const bool more = k <= nrows;
-        float pn0 = 0.f, pn1 = 0.f;
-        if (more) {
-            const float* src = a.dpsi_in + oq;
-            pn0 = __ldg(src + pc0);
-            if (tid < 4) pn1 = __ldg(src + pc1);
-        }
-        oq = step_row<DIR>(oq, nx, N);
-        float fn[9];
-        if (more) load_site(fn, a.g_in + (sa + cx));
-
-        // ---- force from the dpsi(t) ring, then moments and collision
-        const float* rows[5];
-#pragma unroll
-        for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
-        const float pc = a.psi_ref + rows[2][0];
-        float Sx, Sy;
-        force_sums(rows, a, Sx, Sy);
-        float gs[9];
-        const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
-
         const bool out_site = out_col && r >= y0 && r < y1;
-        if (REDUCE && out_site) ms += d;
-
-        // ---- exchange post-collision values with the neighbouring columns
-        exR[r & 1][tid + 1] = make_float4(gs[8], gs[1], gs[5], 0.f);
-        exL[r & 1][tid + 1] = make_float4(gs[7], gs[3], gs[6], 0.f);
-        if (more) {
-            win[(r + 3 * DIR) & 7][tid] = pn0;
-            if (tid < 4) win[(r + 3 * DIR) & 7][BX + tid] = pn1;
-        }
-        // ---- f(t+1) = f*(x - c_i) (Eq. 1) for the own column: the speeds with
-        // c_y = -DIR land in the behind row, c_y = 0 in row r, c_y = +DIR in the
-        // ahead row. The own-column speeds are stored now, the six from the
-        // neighbouring columns after the barrier.
         const int rb = r - DIR, ra = r + DIR;
         const bool st_b = out_col && rb >= y0 && rb < y1;
         const bool st_0 = out_site;
         const bool st_a = out_col && ra >= y0 && ra < y1;
         constexpr int ib = DIR > 0 ? 4 : 2, ia = DIR > 0 ? 2 : 4;   // own speeds with c_y = -DIR, +DIR
-        if (st_b) st_(a.g_out + (sb + cx) + kTileW * ib, gs[ib]);
-        if (st_0) st_(a.g_out + (sc + cx), gs[0]);
-        if (st_a) st_(a.g_out + (sa + cx) + kTileW * ia, gs[ia]);
-        const float own_b = gs[ib], own_0 = gs[0], own_a = gs[ia];
+        float fn[9];
+        float own_b = 0.f, own_0 = 0.f, own_a = 0.f;
+        if (wact) {
+            // ---- prefetch: dpsi row r+3 DIR and the populations of row r+DIR
+            float pn0 = 0.f, pn1 = 0.f;
+            if (more) {
+                const float* src = a.dpsi_in + oq;
+                pn0 = __ldg(src + pc0);
+                if (tid < 4) pn1 = __ldg(src + pc1);
+            }
+            if (more) load_site(fn, a.g_in + (sa + cx));
+
+            // ---- force from the dpsi(t) ring, then moments and collision
+            const float* rows[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
+            const float pc = a.psi_ref + rows[2][0];
+            float Sx, Sy;
+            force_sums(rows, a, Sx, Sy);
+            float gs[9];
+            const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
+            if (REDUCE && out_site) ms += d;
+
+            // ---- exchange post-collision values with the neighbouring columns
+            exR[r & 1][tid + 1] = make_float4(gs[8], gs[1], gs[5], 0.f);
+            exL[r & 1][tid + 1] = make_float4(gs[7], gs[3], gs[6], 0.f);
+            if (more) {
+                win[(r + 3 * DIR) & 7][tid] = pn0;
+                if (tid < 4) win[(r + 3 * DIR) & 7][BX + tid] = pn1;
+            }
+            // ---- f(t+1) = f*(x - c_i) (Eq. 1) for the own column: the speeds with
+            // c_y = -DIR land in the behind row, c_y = 0 in row r, c_y = +DIR in the
+            // ahead row. The own-column speeds are stored now, the six from the
+            // neighbouring columns after the barrier.
+            if (st_b) st_(a.g_out + (sb + cx) + kTileW * ib, gs[ib]);
+            if (st_0) st_(a.g_out + (sc + cx), gs[0]);
+            if (st_a) st_(a.g_out + (sa + cx) + kTileW * ia, gs[ia]);
+            own_b = gs[ib];
+            own_0 = gs[0];
+            own_a = gs[ia];
+        }
+        oq = step_row<DIR>(oq, nx, N);
         __syncthreads();
-        const float4 R = exR[r & 1][tid];       // from column x-1: speeds 8, 1, 5
-        const float4 L = exL[r & 1][tid + 2];   // from column x+1: speeds 7, 3, 6
-        const float Rb = DIR > 0 ? R.x : R.z, Lb = DIR > 0 ? L.x : L.z;
-        const float Ra = DIR > 0 ? R.z : R.x, La = DIR > 0 ? L.z : L.x;
-        if (st_b) {
-            T* o = a.g_out + (sb + cx);
-            st_(o + kTileW * (DIR > 0 ? 7 : 6), Lb);
-            st_(o + kTileW * (DIR > 0 ? 8 : 5), Rb);
+        if (wact) {
+            const float4 R = exR[r & 1][tid];       // from column x-1: speeds 8, 1, 5
+            const float4 L = exL[r & 1][tid + 2];   // from column x+1: speeds 7, 3, 6
+            const float Rb = DIR > 0 ? R.x : R.z, Lb = DIR > 0 ? L.x : L.z;
+            const float Ra = DIR > 0 ? R.z : R.x, La = DIR > 0 ? L.z : L.x;
+            if (st_b) {
+                T* o = a.g_out + (sb + cx);
+                st_(o + kTileW * (DIR > 0 ? 7 : 6), Lb);
+                st_(o + kTileW * (DIR > 0 ? 8 : 5), Rb);
+            }
+            if (st_0) {
+                T* o = a.g_out + (sc + cx);
+                st_(o + kTileW * 1, R.y);
+                st_(o + kTileW * 3, L.y);
+            }
+            if (st_a) {
+                T* o = a.g_out + (sa + cx);
+                st_(o + kTileW * (DIR > 0 ? 6 : 7), La);
+                st_(o + kTileW * (DIR > 0 ? 5 : 8), Ra);
+            }
+            const float gb = own_b + (Rb + Lb);     // behind-group sum into row r-DIR
+            const float g0 = own_0 + (R.y + L.y);   // zero-group sum of row r
+            const float ga = own_a + (Ra + La);     // ahead-group sum into row r+DIR
+            // rho(t+1) of the behind row is complete: (G+ + G0) + G-
+            if (st_b) {
+                const float rho1 = DIR > 0 ? (hb + zb) + gb : (gb + zb) + hb;
+                a.dpsi_out[rb * nx + xc] = dpsi_of(rho1, a);
+            }
+            hb = hc;
+            zb = g0;
+            hc = ga;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = fn[i];
+            if (REDUCE && out_site) {
+                // Sec. 5 energies of state t at (x, r); the dpsi rows r-2..r+2 stay in the
+                // ring until the next iteration overwrites slot (r + 4 DIR) & 7
+                const float* rows[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
+                energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
+                if ((k & 63) == 63) {
+                    d_es += es; d_em += em; d_eb += eb; d_ms += ms;
+                    es = em = eb = ms = 0.f;
+                }
+            }
         }
-        if (st_0) {
-            T* o = a.g_out + (sc + cx);
-            st_(o + kTileW * 1, R.y);
-            st_(o + kTileW * 3, L.y);
-        }
-        if (st_a) {
-            T* o = a.g_out + (sa + cx);
-            st_(o + kTileW * (DIR > 0 ? 6 : 7), La);
-            st_(o + kTileW * (DIR > 0 ? 5 : 8), Ra);
-        }
-        const float gb = own_b + (Rb + Lb);     // behind-group sum into row r-DIR
-        const float g0 = own_0 + (R.y + L.y);   // zero-group sum of row r
-        const float ga = own_a + (Ra + La);     // ahead-group sum into row r+DIR
-        // rho(t+1) of the behind row is complete: (G+ + G0) + G-
-        if (st_b) {
-            const float rho1 = DIR > 0 ? (hb + zb) + gb : (gb + zb) + hb;
-            a.dpsi_out[rb * nx + xc] = dpsi_of(rho1, a);
-        }
-        hb = hc;
-        zb = g0;
-        hc = ga;
         sb = sc;
         sc = sa;
         sa = step_row<DIR>(sa, P, NP);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = fn[i];
-        if (REDUCE && out_site) {
-            // Sec. 5 energies of state t at (x, r); the dpsi rows r-2..r+2 stay in the
-            // ring until the next iteration overwrites slot (r + 4 DIR) & 7
-            energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
-            if ((k & 63) == 63) {
-                d_es += es; d_em += em; d_eb += eb; d_ms += ms;
-                es = em = eb = ms = 0.f;
-            }
-        }
     }
 
     if (REDUCE) {
@@ -262,14 +278,14 @@ __global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / B
 // counter (sched[0]), so a CTA that finishes early takes the next tile
 // instead of waiting for a fixed share; the last CTA to leave resets the
 // counters (sched[1] counts the CTAs that left) for the next launch. The
-// replica's arguments are staged in shared memory once per tile. Plain steps
-// march in alternating directions per row chunk when `alternate` is set (the
-// fields do not depend on the direction); reduction steps march down. With
-// REDUCE each tile's CTA partial (the same block sum k_step forms) goes to
+// replica's arguments are staged in shared memory once per tile. Tiles march
+// down (alternating directions, measured on the 96-replica sweep, gained
+// nothing and raised the register count past the 40-warp budget). With REDUCE
+// each tile's CTA partial (the same block sum k_step forms) goes to
 // tile_partials; k_batch_reduce then sums a replica's partials in the order
 // k_step's last CTA uses, so a replica's fields and trace are bit-identical to
 // running it alone with the same shape.
-template <typename T, int BX, bool REDUCE, bool OM1, bool ALT>
+template <typename T, int BX, bool REDUCE, bool OM1>
 __global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
     k_step_batch(const StepArgs<T>* __restrict__ args, const int4* __restrict__ tiles, int ntiles,
                  double* __restrict__ tile_partials, unsigned int* __restrict__ sched)
@@ -288,7 +304,7 @@ __global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
         if (k >= ntiles) break;
         const int4 tl = tiles[k];                   // (replica, strip, chunk, -)
         double v[4];
-        step_tile<T, BX, REDUCE, OM1, ALT>(sa, tl.y, tl.z, v);
+        step_tile<T, BX, REDUCE, OM1, false>(sa, tl.y, tl.z, v);
         if (REDUCE) {
             block_sum4<BX>(v);
             if (threadIdx.x == 0) {
@@ -502,14 +518,9 @@ cudaError_t launch_batch_bx(const BatchLaunch<T>& b, bool reduce, cudaStream_t s
     };
     cudaError_t e;
     if (reduce)
-        e = b.om1 ? pick(k_step_batch<T, BX, true, true, false>)
-                  : pick(k_step_batch<T, BX, true, false, false>);
-    else if (b.alternate)
-        e = b.om1 ? pick(k_step_batch<T, BX, false, true, true>)
-                  : pick(k_step_batch<T, BX, false, false, true>);
+        e = b.om1 ? pick(k_step_batch<T, BX, true, true>) : pick(k_step_batch<T, BX, true, false>);
     else
-        e = b.om1 ? pick(k_step_batch<T, BX, false, true, false>)
-                  : pick(k_step_batch<T, BX, false, false, false>);
+        e = b.om1 ? pick(k_step_batch<T, BX, false, true>) : pick(k_step_batch<T, BX, false, false>);
     if (e != cudaSuccess || !reduce) return e;
     k_batch_reduce<BX><<<b.nreps, BX, 0, s>>>(b.tile_partials, b.reps, b.trace_every);
     return cudaGetLastError();

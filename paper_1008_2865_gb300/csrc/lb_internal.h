@@ -140,7 +140,6 @@ struct BatchLaunch {
     int trace_every;
     int num_sms;
     unsigned int* sched;       // [2] tile counter and CTA exit counter, zero between launches
-    bool alternate;            // plain steps march in alternating directions per row chunk
 };
 cudaError_t fp32_batch_step(const BatchLaunch<float>& b, bool reduce, cudaStream_t s);
 cudaError_t fp16_batch_step(const BatchLaunch<__half>& b, bool reduce, cudaStream_t s);
