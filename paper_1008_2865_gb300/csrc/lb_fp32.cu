@@ -87,23 +87,16 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     const int nrows = y1 - y0;
     const int txe = min(BX - 2, nx - x0);
     const bool out_col = tid >= 1 && tid <= txe;
-    // A strip narrower than the CTA (the last strip of a row of tiles) needs the
-    // threads up to txe + 1 (the right halo collision) and, for the dpsi ring,
-    // up to txe + 5; a warp holding none of them skips all work and only keeps
-    // the row barriers (warp-uniform).
-    const bool wact = (tid & ~31) <= txe + 5;
     const int xc = wrapi(x0 - 1 + tid, nx);
     const int pc0 = wrapi(x0 - 3 + tid, nx);
     const int pc1 = wrapi(x0 - 3 + BX + (tid & 3), nx);
     const int cx = tcol(xc);
     const int r0 = DIR > 0 ? y0 - 1 : y1;    // first collision row
 
-    if (wact) {
-        for (int rr = r0 - 2; rr <= r0 + 2; ++rr) {
-            const float* src = a.dpsi_in + wrapi(rr, ny) * nx;
-            win[rr & 7][tid] = __ldg(src + pc0);
-            if (tid < 4) win[rr & 7][BX + tid] = __ldg(src + pc1);
-        }
+    for (int rr = r0 - 2; rr <= r0 + 2; ++rr) {
+        const float* src = a.dpsi_in + wrapi(rr, ny) * nx;
+        win[rr & 7][tid] = __ldg(src + pc0);
+        if (tid < 4) win[rr & 7][BX + tid] = __ldg(src + pc1);
     }
     // Row offsets (row * P) of g, periodic, kept incrementally: at the top of
     // iteration r, sb, sc, sa hold rows r-DIR (behind), r, r+DIR (ahead) and oq
@@ -114,7 +107,7 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     int oq = wrapi(r0 + 3 * DIR, ny) * nx;
 
     float f[9];
-    if (wact) load_site(f, a.g_in + (sc + cx));
+    load_site(f, a.g_in + (sc + cx));
     __syncthreads();
 
     // rho(t+1) of a row from its three speed groups (c_y = +1, 0, -1), summed as
@@ -126,105 +119,96 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
 
     for (int k = 0; k <= nrows + 1; ++k) {
         const int r = r0 + DIR * k;
+        // ---- prefetch: dpsi row r+3 DIR and the populations of row r+DIR
         const bool more = k <= nrows;
+        float pn0 = 0.f, pn1 = 0.f;
+        if (more) {
+            const float* src = a.dpsi_in + oq;
+            pn0 = __ldg(src + pc0);
+            if (tid < 4) pn1 = __ldg(src + pc1);
+        }
+        oq = step_row<DIR>(oq, nx, N);
+        float fn[9];
+        if (more) load_site(fn, a.g_in + (sa + cx));
+
+        // ---- force from the dpsi(t) ring, then moments and collision
+        const float* rows[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
+        const float pc = a.psi_ref + rows[2][0];
+        float Sx, Sy;
+        force_sums(rows, a, Sx, Sy);
+        float gs[9];
+        const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
+
         const bool out_site = out_col && r >= y0 && r < y1;
+        if (REDUCE && out_site) ms += d;
+
+        // ---- exchange post-collision values with the neighbouring columns
+        exR[r & 1][tid + 1] = make_float4(gs[8], gs[1], gs[5], 0.f);
+        exL[r & 1][tid + 1] = make_float4(gs[7], gs[3], gs[6], 0.f);
+        if (more) {
+            win[(r + 3 * DIR) & 7][tid] = pn0;
+            if (tid < 4) win[(r + 3 * DIR) & 7][BX + tid] = pn1;
+        }
+        // ---- f(t+1) = f*(x - c_i) (Eq. 1) for the own column: the speeds with
+        // c_y = -DIR land in the behind row, c_y = 0 in row r, c_y = +DIR in the
+        // ahead row. The own-column speeds are stored now, the six from the
+        // neighbouring columns after the barrier.
         const int rb = r - DIR, ra = r + DIR;
         const bool st_b = out_col && rb >= y0 && rb < y1;
         const bool st_0 = out_site;
         const bool st_a = out_col && ra >= y0 && ra < y1;
         constexpr int ib = DIR > 0 ? 4 : 2, ia = DIR > 0 ? 2 : 4;   // own speeds with c_y = -DIR, +DIR
-        float fn[9];
-        float own_b = 0.f, own_0 = 0.f, own_a = 0.f;
-        if (wact) {
-            // ---- prefetch: dpsi row r+3 DIR and the populations of row r+DIR
-            float pn0 = 0.f, pn1 = 0.f;
-            if (more) {
-                const float* src = a.dpsi_in + oq;
-                pn0 = __ldg(src + pc0);
-                if (tid < 4) pn1 = __ldg(src + pc1);
-            }
-            if (more) load_site(fn, a.g_in + (sa + cx));
-
-            // ---- force from the dpsi(t) ring, then moments and collision
-            const float* rows[5];
-#pragma unroll
-            for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
-            const float pc = a.psi_ref + rows[2][0];
-            float Sx, Sy;
-            force_sums(rows, a, Sx, Sy);
-            float gs[9];
-            const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
-            if (REDUCE && out_site) ms += d;
-
-            // ---- exchange post-collision values with the neighbouring columns
-            exR[r & 1][tid + 1] = make_float4(gs[8], gs[1], gs[5], 0.f);
-            exL[r & 1][tid + 1] = make_float4(gs[7], gs[3], gs[6], 0.f);
-            if (more) {
-                win[(r + 3 * DIR) & 7][tid] = pn0;
-                if (tid < 4) win[(r + 3 * DIR) & 7][BX + tid] = pn1;
-            }
-            // ---- f(t+1) = f*(x - c_i) (Eq. 1) for the own column: the speeds with
-            // c_y = -DIR land in the behind row, c_y = 0 in row r, c_y = +DIR in the
-            // ahead row. The own-column speeds are stored now, the six from the
-            // neighbouring columns after the barrier.
-            if (st_b) st_(a.g_out + (sb + cx) + kTileW * ib, gs[ib]);
-            if (st_0) st_(a.g_out + (sc + cx), gs[0]);
-            if (st_a) st_(a.g_out + (sa + cx) + kTileW * ia, gs[ia]);
-            own_b = gs[ib];
-            own_0 = gs[0];
-            own_a = gs[ia];
-        }
-        oq = step_row<DIR>(oq, nx, N);
+        if (st_b) st_(a.g_out + (sb + cx) + kTileW * ib, gs[ib]);
+        if (st_0) st_(a.g_out + (sc + cx), gs[0]);
+        if (st_a) st_(a.g_out + (sa + cx) + kTileW * ia, gs[ia]);
+        const float own_b = gs[ib], own_0 = gs[0], own_a = gs[ia];
         __syncthreads();
-        if (wact) {
-            const float4 R = exR[r & 1][tid];       // from column x-1: speeds 8, 1, 5
-            const float4 L = exL[r & 1][tid + 2];   // from column x+1: speeds 7, 3, 6
-            const float Rb = DIR > 0 ? R.x : R.z, Lb = DIR > 0 ? L.x : L.z;
-            const float Ra = DIR > 0 ? R.z : R.x, La = DIR > 0 ? L.z : L.x;
-            if (st_b) {
-                T* o = a.g_out + (sb + cx);
-                st_(o + kTileW * (DIR > 0 ? 7 : 6), Lb);
-                st_(o + kTileW * (DIR > 0 ? 8 : 5), Rb);
-            }
-            if (st_0) {
-                T* o = a.g_out + (sc + cx);
-                st_(o + kTileW * 1, R.y);
-                st_(o + kTileW * 3, L.y);
-            }
-            if (st_a) {
-                T* o = a.g_out + (sa + cx);
-                st_(o + kTileW * (DIR > 0 ? 6 : 7), La);
-                st_(o + kTileW * (DIR > 0 ? 5 : 8), Ra);
-            }
-            const float gb = own_b + (Rb + Lb);     // behind-group sum into row r-DIR
-            const float g0 = own_0 + (R.y + L.y);   // zero-group sum of row r
-            const float ga = own_a + (Ra + La);     // ahead-group sum into row r+DIR
-            // rho(t+1) of the behind row is complete: (G+ + G0) + G-
-            if (st_b) {
-                const float rho1 = DIR > 0 ? (hb + zb) + gb : (gb + zb) + hb;
-                a.dpsi_out[rb * nx + xc] = dpsi_of(rho1, a);
-            }
-            hb = hc;
-            zb = g0;
-            hc = ga;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = fn[i];
-            if (REDUCE && out_site) {
-                // Sec. 5 energies of state t at (x, r); the dpsi rows r-2..r+2 stay in the
-                // ring until the next iteration overwrites slot (r + 4 DIR) & 7
-                const float* rows[5];
-#pragma unroll
-                for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
-                energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
-                if ((k & 63) == 63) {
-                    d_es += es; d_em += em; d_eb += eb; d_ms += ms;
-                    es = em = eb = ms = 0.f;
-                }
-            }
+        const float4 R = exR[r & 1][tid];       // from column x-1: speeds 8, 1, 5
+        const float4 L = exL[r & 1][tid + 2];   // from column x+1: speeds 7, 3, 6
+        const float Rb = DIR > 0 ? R.x : R.z, Lb = DIR > 0 ? L.x : L.z;
+        const float Ra = DIR > 0 ? R.z : R.x, La = DIR > 0 ? L.z : L.x;
+        if (st_b) {
+            T* o = a.g_out + (sb + cx);
+            st_(o + kTileW * (DIR > 0 ? 7 : 6), Lb);
+            st_(o + kTileW * (DIR > 0 ? 8 : 5), Rb);
         }
+        if (st_0) {
+            T* o = a.g_out + (sc + cx);
+            st_(o + kTileW * 1, R.y);
+            st_(o + kTileW * 3, L.y);
+        }
+        if (st_a) {
+            T* o = a.g_out + (sa + cx);
+            st_(o + kTileW * (DIR > 0 ? 6 : 7), La);
+            st_(o + kTileW * (DIR > 0 ? 5 : 8), Ra);
+        }
+        const float gb = own_b + (Rb + Lb);     // behind-group sum into row r-DIR
+        const float g0 = own_0 + (R.y + L.y);   // zero-group sum of row r
+        const float ga = own_a + (Ra + La);     // ahead-group sum into row r+DIR
+        // rho(t+1) of the behind row is complete: (G+ + G0) + G-
+        if (st_b) {
+            const float rho1 = DIR > 0 ? (hb + zb) + gb : (gb + zb) + hb;
+            a.dpsi_out[rb * nx + xc] = dpsi_of(rho1, a);
+        }
+        hb = hc;
+        zb = g0;
+        hc = ga;
         sb = sc;
         sc = sa;
         sa = step_row<DIR>(sa, P, NP);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = fn[i];
+        if (REDUCE && out_site) {
+            // Sec. 5 energies of state t at (x, r); the dpsi rows r-2..r+2 stay in the
+            // ring until the next iteration overwrites slot (r + 4 DIR) & 7
+            energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
+            if ((k & 63) == 63) {
+                d_es += es; d_em += em; d_eb += eb; d_ms += ms;
+                es = em = eb = ms = 0.f;
+            }
+        }
     }
 
     if (REDUCE) {
@@ -271,6 +255,10 @@ __global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / B
 }
 
 // ---------------------------------------------------------------- batches
+// Tiles of a batch launch are handed out by an atomic counter (true) or by a
+// fixed stride over the work list (false).
+constexpr bool kBatchDynamic = true;
+
 // Several lattices (replicas, each with its own size and couplings) advanced by
 // one launch: a persistent grid takes tiles from a work list, each tile =
 // (replica, strip, row chunk) of that replica's own launch shape, and runs
@@ -292,10 +280,11 @@ __global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
 {
     __shared__ StepArgs<T> sa;
     __shared__ int s_k;
-    for (;;) {
+    for (int it = 0;; ++it) {
         __syncthreads();                            // previous tile done with sa, s_k and the rings
         if (threadIdx.x == 0) {
-            const int k = (int)atomicAdd(&sched[0], 1u);
+            const int k = kBatchDynamic ? (int)atomicAdd(&sched[0], 1u)
+                                        : (int)(blockIdx.x + (unsigned)it * gridDim.x);
             s_k = k;
             if (k < ntiles) sa = args[tiles[k].x];
         }
@@ -313,7 +302,7 @@ __global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
             }
         }
     }
-    if (threadIdx.x == 0) {
+    if (kBatchDynamic && threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(&sched[1], 1u) == gridDim.x - 1) {
             // every CTA has taken its last tile number: reset for the next launch
@@ -349,49 +338,58 @@ __global__ void __launch_bounds__(BX)
 
 // ---------------------------------------------------------------- helpers
 
+// The helpers below cover the lattice row by row (blockIdx.y strides over rows,
+// the threads of a block over the columns of a row), so that no site index is
+// divided by nx.
 template <typename T>
-__global__ void k_delta_init(T* __restrict__ g, float* __restrict__ dpsi,
-                             const double* __restrict__ rho, int nx, int ny, double rho_ref,
-                             double rho0)
+__global__ void __launch_bounds__(256) k_delta_init(T* __restrict__ g, float* __restrict__ dpsi,
+                                                    const double* __restrict__ rho, int nx,
+                                                    int ny, double rho_ref, double inv_rho0,
+                                                    float cpsi)
 {
-    const long long N = (long long)nx * ny;
     const int pitch = g_pitch(nx);
-    const double w[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
-                         1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
-    const double cpsi = -sqrt(rho0) * exp(-rho_ref / rho0);
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
-         s += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(s / nx), x = (int)(s % nx);
-        // f_i(x, 0) = w_i rho_init(x): the fluid at rest
-        T* p = g + (long long)y * pitch + tcol(x);
-        const double d = rho[s] - rho_ref;
+    const float w0 = 4.f / 9.f, w1 = 1.f / 9.f, w2 = 1.f / 36.f;
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        for (int x = blockIdx.x * 256 + threadIdx.x; x < nx; x += gridDim.x * 256) {
+            const size_t s = (size_t)y * nx + x;
+            // f_i(x, 0) = w_i rho_init(x): the fluid at rest, stored as w_i (rho - rho_ref)
+            const double d = rho[s] - rho_ref;
+            const float df = (float)d;
+            T* p = g + (size_t)y * pitch + tcol(x);
+            st_(p, w0 * df);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st_(p + kTileW * i, (float)(w[i] * d));
-        dpsi[s] = (float)cpsi * expm1f((float)(-d / rho0));
+            for (int i = 1; i < 5; ++i) st_(p + kTileW * i, w1 * df);
+#pragma unroll
+            for (int i = 5; i < 9; ++i) st_(p + kTileW * i, w2 * df);
+            dpsi[s] = cpsi * expm1f((float)(-d * inv_rho0));
+        }
     }
 }
 
+// rho = rho_ref + sum_i g_i and u = sum_i c_i g_i / rho (Eqs. 2-3): the sums in
+// FP32 in the order of the step's moments, u by an IEEE FP32 division, stored as
+// doubles (rho in FP64: rho_ref + d).
 template <typename T>
-__global__ void k_delta_fields(const T* __restrict__ g, int nx, int ny, double rho_ref,
-                               double* __restrict__ rho, double* __restrict__ ux,
-                               double* __restrict__ uy)
+__global__ void __launch_bounds__(256) k_delta_fields(const T* __restrict__ g, int nx, int ny,
+                                                      double rho_ref, double* __restrict__ rho,
+                                                      double* __restrict__ ux,
+                                                      double* __restrict__ uy)
 {
-    const long long N = (long long)nx * ny;
     const int pitch = g_pitch(nx);
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
-         s += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(s / nx), x = (int)(s % nx);
-        float f[9];
-        load_site(f, g + (long long)y * pitch + tcol(x));
-        double d = 0.0, jx = 0.0, jy = 0.0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) d += (double)f[i];
-        jx = ((double)f[1] - f[3]) + ((double)f[5] - f[6]) + ((double)f[8] - f[7]);
-        jy = ((double)f[2] - f[4]) + ((double)f[5] + f[6]) - ((double)f[7] + f[8]);
-        const double r = rho_ref + d;
-        if (rho) rho[s] = r;
-        if (ux) ux[s] = jx / r;
-        if (uy) uy[s] = jy / r;
+    const float rref = (float)rho_ref;
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        for (int x = blockIdx.x * 256 + threadIdx.x; x < nx; x += gridDim.x * 256) {
+            float f[9];
+            load_site(f, g + (size_t)y * pitch + tcol(x));
+            const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+            const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+            const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+            const float r = rref + d;
+            const size_t s = (size_t)y * nx + x;
+            if (rho) rho[s] = rho_ref + (double)d;
+            if (ux) ux[s] = (double)__fdiv_rn(jx, r);
+            if (uy) uy[s] = (double)__fdiv_rn(jy, r);
+        }
     }
 }
 
@@ -557,12 +555,21 @@ static int helper_grid(long long n)
     return (int)b;
 }
 
+// Grid of the row-wise helpers: enough blocks per row to cover it, all rows
+// (grid-stride beyond 65535).
+static dim3 row_grid(int nx, int ny)
+{
+    const int bx = (nx + 255) / 256;
+    return dim3((unsigned)(bx < 64 ? bx : 64), (unsigned)(ny < 65535 ? ny : 65535));
+}
+
 template <typename T>
 cudaError_t delta_init(T* g, float* dpsi, const double* rho_init, int nx, int ny, double rho_ref,
                        double rho0, cudaStream_t s)
 {
-    k_delta_init<T><<<helper_grid((long long)nx * ny), 256, 0, s>>>(g, dpsi, rho_init, nx, ny,
-                                                                     rho_ref, rho0);
+    const float cpsi = (float)(-std::sqrt(rho0) * std::exp(-rho_ref / rho0));
+    k_delta_init<T><<<row_grid(nx, ny), 256, 0, s>>>(g, dpsi, rho_init, nx, ny, rho_ref,
+                                                     1.0 / rho0, cpsi);
     return cudaGetLastError();
 }
 
@@ -570,8 +577,7 @@ template <typename T>
 cudaError_t delta_fields(const T* g, int nx, int ny, double rho_ref, double* rho, double* ux,
                          double* uy, cudaStream_t s)
 {
-    k_delta_fields<T><<<helper_grid((long long)nx * ny), 256, 0, s>>>(g, nx, ny, rho_ref, rho, ux,
-                                                                      uy);
+    k_delta_fields<T><<<row_grid(nx, ny), 256, 0, s>>>(g, nx, ny, rho_ref, rho, ux, uy);
     return cudaGetLastError();
 }
 

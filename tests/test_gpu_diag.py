@@ -40,9 +40,14 @@ def test_time_series_match_the_oracle():
         snaps, tr = _series_gpu(prec, rho0, marks)
         s = diag.energy_series(tr, n * n)
         assert np.array_equal(s["t"], s_ref["t"])
-        for key in ("E_over_Eth", "Em_over_Es", "surface_share"):
+        # the GPU's FP64 energy sums add the same site terms as the oracle in another
+        # order (rounding 1e-16 of E); the surface share is a small difference of two
+        # such sums, so it is compared absolutely, the ratios relatively
+        for key in ("E_over_Eth", "Em_over_Es"):
             tol = 1e-12 if prec == "fp64" else 1e-4
             assert np.max(np.abs(s[key] - s_ref[key]) / np.abs(s_ref[key])) <= tol, (prec, key)
+        tol = 1e-12 if prec == "fp64" else 1e-5
+        assert np.max(np.abs(s["surface_share"] - s_ref["surface_share"])) <= tol, prec
         for m in marks:
             got, want = _observables(snaps[m]), _observables(ref[m])
             if prec == "fp64":
