@@ -31,7 +31,6 @@ struct lb_batch {
     int ntiles = 0;
     double* d_partials = nullptr;
     BatchRep* d_reps = nullptr;
-    unsigned int* d_sched = nullptr;        // tile scheduler counters of k_step_batch
     // graph of one period of steps, starting at t % period == 0
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -42,15 +41,13 @@ namespace {
 
 void free_tables(lb_batch* b)
 {
-    void* ptrs[] = {b->d_args[0], b->d_args[1], b->d_tiles, b->d_partials, b->d_reps,
-                    b->d_sched};
+    void* ptrs[] = {b->d_args[0], b->d_args[1], b->d_tiles, b->d_partials, b->d_reps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     b->d_args[0] = b->d_args[1] = nullptr;
     b->d_tiles = nullptr;
     b->d_partials = nullptr;
     b->d_reps = nullptr;
-    b->d_sched = nullptr;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
     cudaGetLastError();
@@ -104,9 +101,7 @@ lb_status build_tables(lb_batch* b)
         cudaMalloc((void**)&b->d_partials, 4 * sizeof(double) * tiles.size()) == cudaSuccess &&
         cudaMalloc((void**)&b->d_reps, sizeof(BatchRep) * info.size()) == cudaSuccess &&
         cudaMemcpy(b->d_reps, info.data(), sizeof(BatchRep) * info.size(),
-                   cudaMemcpyHostToDevice) == cudaSuccess &&
-        cudaMalloc((void**)&b->d_sched, 2 * sizeof(unsigned int)) == cudaSuccess &&
-        cudaMemset(b->d_sched, 0, 2 * sizeof(unsigned int)) == cudaSuccess;
+                   cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_tables(b);
@@ -122,12 +117,12 @@ cudaError_t enqueue_step(const lb_batch* b, cudaStream_t s, long long t, int cur
     if (b->prec == LB_FP32) {
         BatchLaunch<float> L{static_cast<const StepArgs<float>*>(b->d_args[cur]), b->d_tiles,
                              b->ntiles, b->d_partials, b->d_reps, (int)b->reps.size(),
-                             b->block_x, b->om1, b->trace_every, b->num_sms, b->d_sched};
+                             b->block_x, b->om1, b->trace_every, b->num_sms};
         return fp32_batch_step(L, reduce, s);
     }
     BatchLaunch<__half> L{static_cast<const StepArgs<__half>*>(b->d_args[cur]), b->d_tiles,
                           b->ntiles, b->d_partials, b->d_reps, (int)b->reps.size(),
-                          b->block_x, b->om1, b->trace_every, b->num_sms, b->d_sched};
+                          b->block_x, b->om1, b->trace_every, b->num_sms};
     return fp16_batch_step(L, reduce, s);
 }
 

@@ -255,43 +255,28 @@ __global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / B
 }
 
 // ---------------------------------------------------------------- batches
-// Tiles of a batch launch are handed out by an atomic counter (true) or by a
-// fixed stride over the work list (false).
-constexpr bool kBatchDynamic = true;
-
 // Several lattices (replicas, each with its own size and couplings) advanced by
-// one launch: a persistent grid takes tiles from a work list, each tile =
-// (replica, strip, row chunk) of that replica's own launch shape, and runs
-// exactly the per-tile code of k_step. Tiles are handed out by an atomic
-// counter (sched[0]), so a CTA that finishes early takes the next tile
-// instead of waiting for a fixed share; the last CTA to leave resets the
-// counters (sched[1] counts the CTAs that left) for the next launch. The
-// replica's arguments are staged in shared memory once per tile. Tiles march
-// down (alternating directions, measured on the 96-replica sweep, gained
-// nothing and raised the register count past the 40-warp budget). With REDUCE
-// each tile's CTA partial (the same block sum k_step forms) goes to
-// tile_partials; k_batch_reduce then sums a replica's partials in the order
-// k_step's last CTA uses, so a replica's fields and trace are bit-identical to
-// running it alone with the same shape.
+// one launch: a persistent grid strides over a work list of tiles, each tile
+// = (replica, strip, row chunk) of that replica's own launch shape, and runs
+// exactly the per-tile code of k_step. The replica's arguments are staged in
+// shared memory once per tile. Tiles march down. With REDUCE each tile's CTA
+// partial (the same block sum k_step forms) goes to tile_partials;
+// k_batch_reduce then sums a replica's partials in the order k_step's last CTA
+// uses, so a replica's fields and trace are bit-identical to running it alone
+// with the same shape. (Measured on the 96-replica sweep and not kept: tiles
+// handed out by an atomic counter, 1.2% slower; alternating march directions,
+// no gain and more registers than the 40-warp budget allows.)
 template <typename T, int BX, bool REDUCE, bool OM1>
 __global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
     k_step_batch(const StepArgs<T>* __restrict__ args, const int4* __restrict__ tiles, int ntiles,
-                 double* __restrict__ tile_partials, unsigned int* __restrict__ sched)
+                 double* __restrict__ tile_partials)
 {
     __shared__ StepArgs<T> sa;
-    __shared__ int s_k;
-    for (int it = 0;; ++it) {
-        __syncthreads();                            // previous tile done with sa, s_k and the rings
-        if (threadIdx.x == 0) {
-            const int k = kBatchDynamic ? (int)atomicAdd(&sched[0], 1u)
-                                        : (int)(blockIdx.x + (unsigned)it * gridDim.x);
-            s_k = k;
-            if (k < ntiles) sa = args[tiles[k].x];
-        }
-        __syncthreads();
-        const int k = s_k;
-        if (k >= ntiles) break;
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
         const int4 tl = tiles[k];                   // (replica, strip, chunk, -)
+        __syncthreads();                            // previous tile done with sa and smem rings
+        if (threadIdx.x == 0) sa = args[tl.x];
+        __syncthreads();
         double v[4];
         step_tile<T, BX, REDUCE, OM1, false>(sa, tl.y, tl.z, v);
         if (REDUCE) {
@@ -300,15 +285,6 @@ __global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) tile_partials[4 * (size_t)k + q] = v[q];
             }
-        }
-    }
-    if (kBatchDynamic && threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&sched[1], 1u) == gridDim.x - 1) {
-            // every CTA has taken its last tile number: reset for the next launch
-            sched[0] = 0u;
-            sched[1] = 0u;
-            __threadfence();
         }
     }
 }
@@ -510,8 +486,7 @@ cudaError_t launch_batch_bx(const BatchLaunch<T>& b, bool reduce, cudaStream_t s
         long long grid = (long long)per_sm * b.num_sms;
         if (grid > b.ntiles) grid = b.ntiles;
         if (grid < 1) grid = 1;
-        kern<<<(unsigned int)grid, BX, 0, s>>>(b.args, b.tiles, b.ntiles, b.tile_partials,
-                                               b.sched);
+        kern<<<(unsigned int)grid, BX, 0, s>>>(b.args, b.tiles, b.ntiles, b.tile_partials);
         return cudaGetLastError();
     };
     cudaError_t e;

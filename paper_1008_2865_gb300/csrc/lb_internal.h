@@ -139,7 +139,6 @@ struct BatchLaunch {
     bool om1;                  // every replica has omega == 1
     int trace_every;
     int num_sms;
-    unsigned int* sched;       // [2] tile counter and CTA exit counter, zero between launches
 };
 cudaError_t fp32_batch_step(const BatchLaunch<float>& b, bool reduce, cudaStream_t s);
 cudaError_t fp16_batch_step(const BatchLaunch<__half>& b, bool reduce, cudaStream_t s);
