@@ -86,7 +86,7 @@ template <typename T>
 __device__ __forceinline__ void site_f(const T* __restrict__ g, int pitch, int x, int y,
                                        float f[9])
 {
-    load_site(f, g + y * pitch + tcol(x));
+    load_site_xy(f, g, pitch, x, y);
 }
 
 struct AdjArgs {

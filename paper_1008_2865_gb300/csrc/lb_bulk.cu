@@ -160,10 +160,12 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
     const int xu = x0 - 1 + min(tid, TX + 1);    // thread column, unwrapped (-1 .. nx)
     const int ta = (x0 - 1) >> 5;                // first tile of the window, unwrapped
     const int nt = ((x0 + TX) >> 5) - ta + 1;    // tiles in this CTA's window
-    const int gpos = ((xu >> 5) - ta) * kTileElems + (xu & (kTileW - 1));
+    // the thread column's single and pair offsets within the window of tiles
+    const int gps = ((xu >> 5) - ta) * kTileElems + (xu & (kTileW - 1));
+    const int gpp = ((xu >> 5) - ta) * kTileElems + 2 * (xu & (kTileW - 1));
     const int ppos = min(tid, TX + 1) + 3;       // thread column in the dpsi window
     const int xc = x0 - 1 + tid;                 // output column (out_col threads)
-    const int cx = tcol(xc);
+    const int cs = tsingle(xc), cp = tpair(xc);
     const long long limit = a.wait_cycles;
     const uint32_t unit_bytes = (uint32_t)(nt * kTileElems * sizeof(T) + WP * sizeof(float));
 
@@ -226,10 +228,14 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
         }
         // ---- unit it completes population row r and dpsi row r+2
         fail |= !mbar_wait_bounded(&bars[it % NB], (uint32_t)((it / NB) & 1), limit);
-        const T* gr = gring + (it % NG) * WG + gpos;
+        const T* gr = gring + (it % NG) * WG;
         float f[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = lds_(gr + kTileW * i);
+        f[0] = lds_(gr + gps + kPop0);
+        f[2] = lds_(gr + gps + kPop2);
+        f[4] = lds_(gr + gps + kPop4);
+        lds_pair(gr + gpp + kPair13, f[1], f[3]);
+        lds_pair(gr + gpp + kPair56, f[5], f[6]);
+        lds_pair(gr + gpp + kPair78, f[7], f[8]);
         // ---- dpsi rows r-2 .. r+2 (ring slots it .. it+4)
         const float* rows[5];
 #pragma unroll
@@ -268,22 +274,16 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
         const float4 R = exR[it & 1][tid];
         const float4 L = exL[it & 1][tid + 2];
         if (st_m) {
-            T* o = a.g_out + (s0 + cx);
-            st_(o + kTileW * 4, gs[4]);
-            st_(o + kTileW * 7, L.x);
-            st_(o + kTileW * 8, R.x);
+            st_(a.g_out + (s0 + cs + kPop4), gs[4]);
+            st_pair(a.g_out + (s0 + cp + kPair78), L.x, R.x);
         }
         if (st_0) {
-            T* o = a.g_out + (s1 + cx);
-            st_(o, gs[0]);
-            st_(o + kTileW * 1, R.y);
-            st_(o + kTileW * 3, L.y);
+            st_(a.g_out + (s1 + cs + kPop0), gs[0]);
+            st_pair(a.g_out + (s1 + cp + kPair13), R.y, L.y);
         }
         if (st_p) {
-            T* o = a.g_out + (s2 + cx);
-            st_(o + kTileW * 2, gs[2]);
-            st_(o + kTileW * 5, R.z);
-            st_(o + kTileW * 6, L.z);
+            st_(a.g_out + (s2 + cs + kPop2), gs[2]);
+            st_pair(a.g_out + (s2 + cp + kPair56), R.z, L.z);
         }
         acc_m += gs[4] + (R.x + L.x);
         acc_0 += gs[0] + (R.y + L.y);

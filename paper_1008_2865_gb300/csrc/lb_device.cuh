@@ -14,6 +14,39 @@ __device__ __forceinline__ void st_(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st_(__half* p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ float lds_(const float* p) { return *p; }
 __device__ __forceinline__ float lds_(const __half* p) { return __half2float(*p); }
+// a pair of adjacent populations (lb_internal.h): one 8-byte or 4-byte access
+__device__ __forceinline__ void ldg_pair(const float* p, float& a, float& b)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ldg_pair(const __half* p, float& a, float& b)
+{
+    const float2 v = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void lds_pair(const float* p, float& a, float& b)
+{
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void lds_pair(const __half* p, float& a, float& b)
+{
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void st_pair(float* p, float a, float b)
+{
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void st_pair(__half* p, float a, float b)
+{
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+}
 
 __device__ __forceinline__ int wrapi(int a, int n)
 {
@@ -21,16 +54,31 @@ __device__ __forceinline__ int wrapi(int a, int n)
     return a < 0 ? a + n : a;
 }
 
-// Offset of column x within a row of the tiled population layout (lb_internal.h):
-// population i of site (x, y) is at y * pitch + tcol(x) + 32 i.
-__device__ __forceinline__ int tcol(int x) { return (x >> 5) * kTileElems + (x & (kTileW - 1)); }
+// Offsets of column x within a row of the tiled population layout
+// (lb_internal.h): populations 0, 2, 4 of site (x, y) are at y * pitch +
+// tsingle(x) + kPop0 / kPop2 / kPop4, the pairs at y * pitch + tpair(x) +
+// kPair13 / kPair56 / kPair78.
+__device__ __forceinline__ int tsingle(int x) { return (x >> 5) * kTileElems + (x & (kTileW - 1)); }
+__device__ __forceinline__ int tpair(int x) { return (x >> 5) * kTileElems + 2 * (x & (kTileW - 1)); }
 
-// The 9 populations of one site, p = g + y * pitch + tcol(x).
+// The 9 populations of one site from a row pointer and the column's offsets.
 template <typename T>
-__device__ __forceinline__ void load_site(float f[9], const T* __restrict__ p)
+__device__ __forceinline__ void load_site(float f[9], const T* __restrict__ row, int cs, int cp)
 {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = ldg_(p + kTileW * i);
+    f[0] = ldg_(row + cs + kPop0);
+    f[2] = ldg_(row + cs + kPop2);
+    f[4] = ldg_(row + cs + kPop4);
+    ldg_pair(row + cp + kPair13, f[1], f[3]);
+    ldg_pair(row + cp + kPair56, f[5], f[6]);
+    ldg_pair(row + cp + kPair78, f[7], f[8]);
+}
+
+// The 9 populations of site (x, y) of a tiled buffer with `pitch` elements per row.
+template <typename T>
+__device__ __forceinline__ void load_site_xy(float f[9], const T* __restrict__ g, int pitch, int x,
+                                             int y)
+{
+    load_site(f, g + (size_t)y * pitch, tsingle(x), tpair(x));
 }
 
 // Two-belt force sums of Eq. FORCE in pair form. r[k] points at the stencil

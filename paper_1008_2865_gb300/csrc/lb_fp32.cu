@@ -75,7 +75,7 @@ __device__ __forceinline__ int step_row(int off, int stride, int total)
 template <typename T, int BX, bool REDUCE, bool OM1, int DIR>
 __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int by, double v[4],
                                               float (*win)[BX + 4], float4 (*exR)[BX + 2],
-                                              float4 (*exL)[BX + 2])
+                                              float4 (*exL)[BX + 2], double* eacc)
 {
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     const int xc = wrapi(x0 - 1 + tid, nx);
     const int pc0 = wrapi(x0 - 3 + tid, nx);
     const int pc1 = wrapi(x0 - 3 + BX + (tid & 3), nx);
-    const int cx = tcol(xc);
+    const int cs = tsingle(xc), cp = tpair(xc);   // the column's single and pair offsets
     const int r0 = DIR > 0 ? y0 - 1 : y1;    // first collision row
 
     for (int rr = r0 - 2; rr <= r0 + 2; ++rr) {
@@ -107,15 +107,21 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     int oq = wrapi(r0 + 3 * DIR, ny) * nx;
 
     float f[9];
-    load_site(f, a.g_in + (sc + cx));
+    load_site(f, a.g_in + sc, cs, cp);
     __syncthreads();
 
     // rho(t+1) of a row from its three speed groups (c_y = +1, 0, -1), summed as
     // (G+ + G0) + G- whatever the direction: hb = ahead-group sum of the behind
     // row, zb = zero-group sum of the behind row, hc = ahead-group sum of row r.
     float hb = 0.f, zb = 0.f, hc = 0.f;
+    // energy/mass sums: FP32 in registers for up to 64 rows, then added into this
+    // thread's FP64 slots in shared memory (eacc[q * BX + tid]), which keeps the
+    // FP64 accumulators out of the registers of the row loop
     float es = 0.f, em = 0.f, eb = 0.f, ms = 0.f;
-    double d_es = 0.0, d_em = 0.0, d_eb = 0.0, d_ms = 0.0;
+    if (REDUCE) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) eacc[q * BX + tid] = 0.0;
+    }
 
     for (int k = 0; k <= nrows + 1; ++k) {
         const int r = r0 + DIR * k;
@@ -129,7 +135,7 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
         }
         oq = step_row<DIR>(oq, nx, N);
         float fn[9];
-        if (more) load_site(fn, a.g_in + (sa + cx));
+        if (more) load_site(fn, a.g_in + sa, cs, cp);
 
         // ---- force from the dpsi(t) ring, then moments and collision
         const float* rows[5];
@@ -160,29 +166,27 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
         const bool st_0 = out_site;
         const bool st_a = out_col && ra >= y0 && ra < y1;
         constexpr int ib = DIR > 0 ? 4 : 2, ia = DIR > 0 ? 2 : 4;   // own speeds with c_y = -DIR, +DIR
-        if (st_b) st_(a.g_out + (sb + cx) + kTileW * ib, gs[ib]);
-        if (st_0) st_(a.g_out + (sc + cx), gs[0]);
-        if (st_a) st_(a.g_out + (sa + cx) + kTileW * ia, gs[ia]);
+        constexpr int ob = DIR > 0 ? kPop4 : kPop2, oa = DIR > 0 ? kPop2 : kPop4;
+        if (st_b) st_(a.g_out + (sb + cs + ob), gs[ib]);
+        if (st_0) st_(a.g_out + (sc + cs + kPop0), gs[0]);
+        if (st_a) st_(a.g_out + (sa + cs + oa), gs[ia]);
         const float own_b = gs[ib], own_0 = gs[0], own_a = gs[ia];
         __syncthreads();
         const float4 R = exR[r & 1][tid];       // from column x-1: speeds 8, 1, 5
         const float4 L = exL[r & 1][tid + 2];   // from column x+1: speeds 7, 3, 6
         const float Rb = DIR > 0 ? R.x : R.z, Lb = DIR > 0 ? L.x : L.z;
         const float Ra = DIR > 0 ? R.z : R.x, La = DIR > 0 ? L.z : L.x;
+        // the two values from the neighbouring columns form one pair of the layout:
+        // behind row (7, 8) = (L, R) marching down, (5, 6) = (R, L) marching up;
+        // row r (1, 3) = (R, L); ahead row (5, 6) = (R, L) down, (7, 8) = (L, R) up
         if (st_b) {
-            T* o = a.g_out + (sb + cx);
-            st_(o + kTileW * (DIR > 0 ? 7 : 6), Lb);
-            st_(o + kTileW * (DIR > 0 ? 8 : 5), Rb);
+            if (DIR > 0) st_pair(a.g_out + (sb + cp + kPair78), Lb, Rb);
+            else st_pair(a.g_out + (sb + cp + kPair56), Rb, Lb);
         }
-        if (st_0) {
-            T* o = a.g_out + (sc + cx);
-            st_(o + kTileW * 1, R.y);
-            st_(o + kTileW * 3, L.y);
-        }
+        if (st_0) st_pair(a.g_out + (sc + cp + kPair13), R.y, L.y);
         if (st_a) {
-            T* o = a.g_out + (sa + cx);
-            st_(o + kTileW * (DIR > 0 ? 6 : 7), La);
-            st_(o + kTileW * (DIR > 0 ? 5 : 8), Ra);
+            if (DIR > 0) st_pair(a.g_out + (sa + cp + kPair56), Ra, La);
+            else st_pair(a.g_out + (sa + cp + kPair78), La, Ra);
         }
         const float gb = own_b + (Rb + Lb);     // behind-group sum into row r-DIR
         const float g0 = own_0 + (R.y + L.y);   // zero-group sum of row r
@@ -205,17 +209,20 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
             // ring until the next iteration overwrites slot (r + 4 DIR) & 7
             energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
             if ((k & 63) == 63) {
-                d_es += es; d_em += em; d_eb += eb; d_ms += ms;
+                eacc[0 * BX + tid] += es;
+                eacc[1 * BX + tid] += em;
+                eacc[2 * BX + tid] += eb;
+                eacc[3 * BX + tid] += ms;
                 es = em = eb = ms = 0.f;
             }
         }
     }
 
     if (REDUCE) {
-        v[0] = d_es + es;
-        v[1] = d_em + em;
-        v[2] = d_eb + eb;
-        v[3] = d_ms + ms;
+        v[0] = eacc[0 * BX + tid] + es;
+        v[1] = eacc[1 * BX + tid] + em;
+        v[2] = eacc[2 * BX + tid] + eb;
+        v[3] = eacc[3 * BX + tid] + ms;
     }
 }
 
@@ -232,10 +239,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, 
     __shared__ float win[8][BX + 4];          // dpsi(t) rows, slot = row & 7
     __shared__ float4 exR[2][BX + 2];        // right-moving f*: speeds 8, 1, 5 (cy = -1, 0, +1)
     __shared__ float4 exL[2][BX + 2];        // left-moving f*: speeds 7, 3, 6
+    __shared__ double eacc[REDUCE ? 4 * BX : 1];   // FP64 energy/mass slots of the threads
     if (ALTERNATE && !REDUCE && alternate && (by & 1))
-        step_tile_dir<T, BX, REDUCE, OM1, -1>(a, bx, by, v, win, exR, exL);
+        step_tile_dir<T, BX, REDUCE, OM1, -1>(a, bx, by, v, win, exR, exL, eacc);
     else
-        step_tile_dir<T, BX, REDUCE, OM1, +1>(a, bx, by, v, win, exR, exL);
+        step_tile_dir<T, BX, REDUCE, OM1, +1>(a, bx, by, v, win, exR, exL, eacc);
 }
 
 template <typename T, int BX, bool REDUCE, bool OM1>
@@ -331,12 +339,14 @@ __global__ void __launch_bounds__(256) k_delta_init(T* __restrict__ g, float* __
             // f_i(x, 0) = w_i rho_init(x): the fluid at rest, stored as w_i (rho - rho_ref)
             const double d = rho[s] - rho_ref;
             const float df = (float)d;
-            T* p = g + (size_t)y * pitch + tcol(x);
-            st_(p, w0 * df);
-#pragma unroll
-            for (int i = 1; i < 5; ++i) st_(p + kTileW * i, w1 * df);
-#pragma unroll
-            for (int i = 5; i < 9; ++i) st_(p + kTileW * i, w2 * df);
+            T* row = g + (size_t)y * pitch;
+            const int cs = tsingle(x), cp = tpair(x);
+            st_(row + cs + kPop0, w0 * df);
+            st_(row + cs + kPop2, w1 * df);
+            st_(row + cs + kPop4, w1 * df);
+            st_pair(row + cp + kPair13, w1 * df, w1 * df);
+            st_pair(row + cp + kPair56, w2 * df, w2 * df);
+            st_pair(row + cp + kPair78, w2 * df, w2 * df);
             dpsi[s] = cpsi * expm1f((float)(-d * inv_rho0));
         }
     }
@@ -356,7 +366,7 @@ __global__ void __launch_bounds__(256) k_delta_fields(const T* __restrict__ g, i
     for (int y = blockIdx.y; y < ny; y += gridDim.y) {
         for (int x = blockIdx.x * 256 + threadIdx.x; x < nx; x += gridDim.x * 256) {
             float f[9];
-            load_site(f, g + (size_t)y * pitch + tcol(x));
+            load_site_xy(f, g, pitch, x, y);
             const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
             const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
             const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
@@ -397,7 +407,7 @@ __global__ void __launch_bounds__(256) k_delta_energy(const T* __restrict__ g,
         v[1] += 0.5 * pc * b2;
         v[2] += (double)a.half_A1 * pc * pc;
         float f[9];
-        load_site(f, g + (long long)y * a.pitch + tcol(x));
+        load_site_xy(f, g, a.pitch, x, y);
         double d = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) d += (double)f[i];
