@@ -202,8 +202,6 @@ template <typename T>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A,
                                                               const T* __restrict__ gT)
 {
-    pdl_trigger();
-    pdl_wait();
     const StepArgs<float>& a = A.a;
     const int nx = a.nx, ny = a.ny, N = (int)a.N;
     double v[4] = {0.0, 0.0, 0.0, 0.0};   // E, misfit, dE/dG1, dE/dG2
@@ -246,8 +244,6 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A,
 
 __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
 {
-    pdl_trigger();
-    pdl_wait();       // l(t+1) from the previous pass B
     const StepArgs<float>& a = A.a;
     const int nx = a.nx, ny = a.ny, N = (int)a.N;
     const float om = a.omega;
@@ -311,8 +307,6 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
 
 __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_b(const AdjArgs A)
 {
-    pdl_trigger();
-    pdl_wait();       // Q, j-bar, rho-bar of pass A
     const StepArgs<float>& a = A.a;
     const int nx = a.nx, ny = a.ny, N = (int)a.N;
     const float omc = a.omc;
@@ -341,8 +335,6 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_b(const AdjArgs A)
 __global__ void k_adj_grad_init(const float* __restrict__ lam, int N, float w0, float w1, float w2,
                                 double* __restrict__ out)
 {
-    pdl_trigger();
-    pdl_wait();
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
         const double g = (double)w0 * lam[s] +
                          (double)w1 * (((double)lam[N + s] + lam[2 * N + s]) +
@@ -502,10 +494,8 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
     A.dpsi = s->dpsi[s->cur];
     A.lam = lamA;
     A.acc = acc;             // acc[0..3] = E, misfit, dE/dG1, dE/dG2
-    if (launch_pdl(k_adj_terminal<float>, dim3(grid), dim3(kAdjThreads), 0, st, A, A.g) !=
-            cudaSuccess ||
-        cudaGetLastError() != cudaSuccess)
-        return fail();
+    k_adj_terminal<float><<<grid, kAdjThreads, 0, st>>>(A, A.g);
+    if (cudaGetLastError() != cudaSuccess) return fail();
 
     // ---- reverse over the segments. Segment k (states kC .. kC + n - 1) is
     // recomputed from its checkpoint into segment buffer k & 1 on the second
@@ -548,10 +538,9 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
             A.dpsi = state + GE;
             A.lam_next = lamA;
             A.lam = lamB;
-            if (launch_pdl(k_adj_pass_a, dim3(grid), dim3(kAdjThreads), 0, st, A) != cudaSuccess ||
-                launch_pdl(k_adj_pass_b, dim3(grid), dim3(kAdjThreads), 0, st, A) != cudaSuccess ||
-                cudaGetLastError() != cudaSuccess)
-                return fail();
+            k_adj_pass_a<<<grid, kAdjThreads, 0, st>>>(A);
+            k_adj_pass_b<<<grid, kAdjThreads, 0, st>>>(A);
+            if (cudaGetLastError() != cudaSuccess) return fail();
             float* tmp = lamA;
             lamA = lamB;
             lamB = tmp;
@@ -559,10 +548,8 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
         if (cudaEventRecord(ev_free[k & 1], st) != cudaSuccess) return fail();
     }
     double* gout = grad_on_dev ? grad_rho : grad_dev;
-    if (launch_pdl(k_adj_grad_init, dim3(adj_grid(N)), dim3(kAdjThreads), 0, st,
-                   (const float*)lamA, N, A.a.w0, A.a.w1, A.a.w2, gout) != cudaSuccess ||
-        cudaGetLastError() != cudaSuccess)
-        return fail();
+    k_adj_grad_init<<<adj_grid(N), kAdjThreads, 0, st>>>(lamA, N, A.a.w0, A.a.w1, A.a.w2, gout);
+    if (cudaGetLastError() != cudaSuccess) return fail();
     double h[8];
     if (cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail();
     if (!grad_on_dev &&

@@ -146,8 +146,6 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
     __shared__ float4 exR[2][BX + 2];        // right-moving f*: speeds 8, 1, 5
     __shared__ float4 exL[2][BX + 2];        // left-moving f*: speeds 7, 3, 6
 
-    pdl_trigger();
-    pdl_wait();                                  // the previous step's populations and psi
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
     const int P = a.pitch;
@@ -330,8 +328,8 @@ cudaError_t launch_bulk(const StepArgs<T>& a, int rows, cudaStream_t s)
         __atomic_fetch_or(&configured, bit, __ATOMIC_RELEASE);
     }
     dim3 grid((a.nx + G::TX - 1) / G::TX, (a.ny + rows - 1) / rows);
-    e = launch_pdl(kern, grid, dim3(BX), smem, s, a);
-    return e != cudaSuccess ? e : cudaGetLastError();
+    kern<<<grid, BX, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename T, int BX>

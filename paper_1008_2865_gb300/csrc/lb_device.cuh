@@ -6,42 +6,6 @@
 #include "lb_internal.h"
 
 namespace lbsc {
-
-// Programmatic dependent launch. A kernel launched with launch_pdl may start
-// while the previous kernel on its stream is still running; pdl_wait() (at the
-// top of the kernel, before it reads anything the previous kernel wrote)
-// blocks until that kernel has completed and its writes are visible, and
-// pdl_trigger() lets the next kernel start launching once every CTA of this one
-// has called it or exited. Each CTA triggers on entry: the next kernel's CTAs
-// then become resident only after this kernel's last CTA has been scheduled,
-// so they never take the place of a CTA this kernel still has to run, and they
-// wait on the SMs instead of being launched after this kernel drains. Without
-// the launch attribute both instructions are no-ops.
-namespace dev {
-__device__ __forceinline__ void pdl_trigger()
-{
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-}  // namespace dev
-
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                       Args&&... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
-
 namespace dev {
 
 __device__ __forceinline__ float ldg_(const float* p) { return __ldg(p); }

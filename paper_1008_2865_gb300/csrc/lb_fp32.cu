@@ -250,8 +250,6 @@ template <typename T, int BX, bool REDUCE, bool OM1>
 __global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / BX)
     k_step(const StepArgs<T> a, bool alternate)
 {
-    pdl_trigger();
-    pdl_wait();       // the previous step's populations and psi
     double v[4];
     step_tile<T, BX, REDUCE, OM1, true>(a, blockIdx.x, blockIdx.y, v, alternate);
     if (REDUCE) {
@@ -282,8 +280,6 @@ __global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
                  double* __restrict__ tile_partials)
 {
     __shared__ StepArgs<T> sa;
-    pdl_trigger();
-    pdl_wait();       // the previous step of every replica
     for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
         const int4 tl = tiles[k];                   // (replica, strip, chunk, -)
         __syncthreads();                            // previous tile done with sa and smem rings
@@ -309,8 +305,6 @@ __global__ void __launch_bounds__(BX)
     k_batch_reduce(const double* __restrict__ tile_partials, const BatchRep* __restrict__ reps,
                    int trace_every)
 {
-    pdl_trigger();
-    pdl_wait();       // the tile partials of the reduction step
     const BatchRep r = reps[blockIdx.x];
     double w[4] = {0.0, 0.0, 0.0, 0.0};
     for (int j = threadIdx.x; j < r.ntiles; j += BX) {
@@ -450,14 +444,14 @@ cudaError_t launch_step_bx(const StepArgs<T>& a, Fp32Launch L, bool reduce, cuda
     // Alternating march directions only pay when the state does not fit in L2
     // (measured: 2% slower at 1024^2, faster from 2048^2 on).
     const bool alt = (long long)a.N * 80 > (128LL << 20);
-    cudaError_t e;
-    if (reduce)
-        e = om1 ? launch_pdl(k_step<T, BX, true, true>, grid, BX, 0, s, a, false)
-                : launch_pdl(k_step<T, BX, true, false>, grid, BX, 0, s, a, false);
-    else
-        e = om1 ? launch_pdl(k_step<T, BX, false, true>, grid, BX, 0, s, a, alt)
-                : launch_pdl(k_step<T, BX, false, false>, grid, BX, 0, s, a, alt);
-    return e != cudaSuccess ? e : cudaGetLastError();
+    if (reduce) {
+        if (om1) k_step<T, BX, true, true><<<grid, BX, 0, s>>>(a, false);
+        else k_step<T, BX, true, false><<<grid, BX, 0, s>>>(a, false);
+    } else {
+        if (om1) k_step<T, BX, false, true><<<grid, BX, 0, s>>>(a, alt);
+        else k_step<T, BX, false, false><<<grid, BX, 0, s>>>(a, alt);
+    }
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -502,9 +496,8 @@ cudaError_t launch_batch_bx(const BatchLaunch<T>& b, bool reduce, cudaStream_t s
         long long grid = (long long)per_sm * b.num_sms;
         if (grid > b.ntiles) grid = b.ntiles;
         if (grid < 1) grid = 1;
-        e = launch_pdl(kern, dim3((unsigned int)grid), dim3(BX), 0, s, b.args, b.tiles, b.ntiles,
-                       b.tile_partials);
-        return e != cudaSuccess ? e : cudaGetLastError();
+        kern<<<(unsigned int)grid, BX, 0, s>>>(b.args, b.tiles, b.ntiles, b.tile_partials);
+        return cudaGetLastError();
     };
     cudaError_t e;
     if (reduce)
@@ -512,9 +505,8 @@ cudaError_t launch_batch_bx(const BatchLaunch<T>& b, bool reduce, cudaStream_t s
     else
         e = b.om1 ? pick(k_step_batch<T, BX, false, true>) : pick(k_step_batch<T, BX, false, false>);
     if (e != cudaSuccess || !reduce) return e;
-    e = launch_pdl(k_batch_reduce<BX>, dim3(b.nreps), dim3(BX), 0, s, b.tile_partials, b.reps,
-                   b.trace_every);
-    return e != cudaSuccess ? e : cudaGetLastError();
+    k_batch_reduce<BX><<<b.nreps, BX, 0, s>>>(b.tile_partials, b.reps, b.trace_every);
+    return cudaGetLastError();
 }
 
 template <typename T>
