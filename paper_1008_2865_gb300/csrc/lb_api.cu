@@ -585,7 +585,7 @@ struct SavedHeader {
     double rho_ref;
     long long payload;        // bytes after the header
 };
-constexpr int kSaveVersion = 3;   // 3: tiled populations of state t, pairs side by side
+constexpr int kSaveVersion = 3;   // 3: tiled populations of state t (FP32 pairs side by side)
 
 size_t payload_bytes(const lb_state* s)
 {

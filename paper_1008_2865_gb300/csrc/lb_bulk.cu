@@ -161,11 +161,12 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
     const int ta = (x0 - 1) >> 5;                // first tile of the window, unwrapped
     const int nt = ((x0 + TX) >> 5) - ta + 1;    // tiles in this CTA's window
     // the thread column's single and pair offsets within the window of tiles
+    using TL = Tile<T>;
     const int gps = ((xu >> 5) - ta) * kTileElems + (xu & (kTileW - 1));
-    const int gpp = ((xu >> 5) - ta) * kTileElems + 2 * (xu & (kTileW - 1));
+    const int gpp = ((xu >> 5) - ta) * kTileElems + (TL::kPaired ? 2 : 1) * (xu & (kTileW - 1));
     const int ppos = min(tid, TX + 1) + 3;       // thread column in the dpsi window
     const int xc = x0 - 1 + tid;                 // output column (out_col threads)
-    const int cs = tsingle(xc), cp = tpair(xc);
+    const int cs = tsingle(xc), cp = tpair<T>(xc);
     const long long limit = a.wait_cycles;
     const uint32_t unit_bytes = (uint32_t)(nt * kTileElems * sizeof(T) + WP * sizeof(float));
 
@@ -230,12 +231,12 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
         fail |= !mbar_wait_bounded(&bars[it % NB], (uint32_t)((it / NB) & 1), limit);
         const T* gr = gring + (it % NG) * WG;
         float f[9];
-        f[0] = lds_(gr + gps + kPop0);
-        f[2] = lds_(gr + gps + kPop2);
-        f[4] = lds_(gr + gps + kPop4);
-        lds_pair(gr + gpp + kPair13, f[1], f[3]);
-        lds_pair(gr + gpp + kPair56, f[5], f[6]);
-        lds_pair(gr + gpp + kPair78, f[7], f[8]);
+        f[0] = lds_(gr + gps + TL::P0);
+        f[2] = lds_(gr + gps + TL::P2);
+        f[4] = lds_(gr + gps + TL::P4);
+        lds2<TL::A13, TL::B13>(gr + gpp, f[1], f[3]);
+        lds2<TL::A56, TL::B56>(gr + gpp, f[5], f[6]);
+        lds2<TL::A78, TL::B78>(gr + gpp, f[7], f[8]);
         // ---- dpsi rows r-2 .. r+2 (ring slots it .. it+4)
         const float* rows[5];
 #pragma unroll
@@ -274,16 +275,16 @@ __global__ void __launch_bounds__(BX) k_step_bulk(const StepArgs<T> a)
         const float4 R = exR[it & 1][tid];
         const float4 L = exL[it & 1][tid + 2];
         if (st_m) {
-            st_(a.g_out + (s0 + cs + kPop4), gs[4]);
-            st_pair(a.g_out + (s0 + cp + kPair78), L.x, R.x);
+            st_(a.g_out + (s0 + cs + TL::P4), gs[4]);
+            st2<TL::A78, TL::B78>(a.g_out + (s0 + cp), L.x, R.x);
         }
         if (st_0) {
-            st_(a.g_out + (s1 + cs + kPop0), gs[0]);
-            st_pair(a.g_out + (s1 + cp + kPair13), R.y, L.y);
+            st_(a.g_out + (s1 + cs + TL::P0), gs[0]);
+            st2<TL::A13, TL::B13>(a.g_out + (s1 + cp), R.y, L.y);
         }
         if (st_p) {
-            st_(a.g_out + (s2 + cs + kPop2), gs[2]);
-            st_pair(a.g_out + (s2 + cp + kPair56), R.z, L.z);
+            st_(a.g_out + (s2 + cs + TL::P2), gs[2]);
+            st2<TL::A56, TL::B56>(a.g_out + (s2 + cp), R.z, L.z);
         }
         acc_m += gs[4] + (R.x + L.x);
         acc_0 += gs[0] + (R.y + L.y);

@@ -54,23 +54,76 @@ __device__ __forceinline__ int wrapi(int a, int n)
     return a < 0 ? a + n : a;
 }
 
-// Offsets of column x within a row of the tiled population layout
-// (lb_internal.h): populations 0, 2, 4 of site (x, y) are at y * pitch +
-// tsingle(x) + kPop0 / kPop2 / kPop4, the pairs at y * pitch + tpair(x) +
-// kPair13 / kPair56 / kPair78.
+// Element offsets within a tile of the tiled population layout (lb_internal.h),
+// relative to the column offsets tsingle(x) (populations 0, 2, 4) and tpair(x)
+// (the pairs (1, 3), (5, 6), (7, 8); A and B are a pair's first and second
+// member).
+template <typename T>
+struct Tile;
+template <>
+struct Tile<float> {   // paired: a pair is two adjacent elements
+    static constexpr bool kPaired = true;
+    static constexpr int P0 = 0, P2 = 32, P4 = 64;
+    static constexpr int A13 = 96, B13 = 97, A56 = 160, B56 = 161, A78 = 224, B78 = 225;
+};
+template <>
+struct Tile<__half> {  // nine runs of 32: population i at 32 i
+    static constexpr bool kPaired = false;
+    static constexpr int P0 = 0, P2 = 64, P4 = 128;
+    static constexpr int A13 = 32, B13 = 96, A56 = 160, B56 = 192, A78 = 224, B78 = 256;
+};
 __device__ __forceinline__ int tsingle(int x) { return (x >> 5) * kTileElems + (x & (kTileW - 1)); }
-__device__ __forceinline__ int tpair(int x) { return (x >> 5) * kTileElems + 2 * (x & (kTileW - 1)); }
+template <typename T>
+__device__ __forceinline__ int tpair(int x)
+{
+    return (x >> 5) * kTileElems + (Tile<T>::kPaired ? 2 : 1) * (x & (kTileW - 1));
+}
 
-// The 9 populations of one site from a row pointer and the column's offsets.
+// A pair (members at p + OA and p + OB) from global memory, shared memory, or
+// into global memory: one access in the paired layout, two otherwise.
+template <int OA, int OB, typename T>
+__device__ __forceinline__ void ld2(const T* __restrict__ p, float& a, float& b)
+{
+    if (Tile<T>::kPaired) {
+        ldg_pair(p + OA, a, b);
+    } else {
+        a = ldg_(p + OA);
+        b = ldg_(p + OB);
+    }
+}
+template <int OA, int OB, typename T>
+__device__ __forceinline__ void lds2(const T* p, float& a, float& b)
+{
+    if (Tile<T>::kPaired) {
+        lds_pair(p + OA, a, b);
+    } else {
+        a = lds_(p + OA);
+        b = lds_(p + OB);
+    }
+}
+template <int OA, int OB, typename T>
+__device__ __forceinline__ void st2(T* p, float a, float b)
+{
+    if (Tile<T>::kPaired) {
+        st_pair(p + OA, a, b);
+    } else {
+        st_(p + OA, a);
+        st_(p + OB, b);
+    }
+}
+
+// The 9 populations of one site from a row pointer and the column's offsets
+// cs = tsingle(x), cp = tpair<T>(x).
 template <typename T>
 __device__ __forceinline__ void load_site(float f[9], const T* __restrict__ row, int cs, int cp)
 {
-    f[0] = ldg_(row + cs + kPop0);
-    f[2] = ldg_(row + cs + kPop2);
-    f[4] = ldg_(row + cs + kPop4);
-    ldg_pair(row + cp + kPair13, f[1], f[3]);
-    ldg_pair(row + cp + kPair56, f[5], f[6]);
-    ldg_pair(row + cp + kPair78, f[7], f[8]);
+    using L = Tile<T>;
+    f[0] = ldg_(row + cs + L::P0);
+    f[2] = ldg_(row + cs + L::P2);
+    f[4] = ldg_(row + cs + L::P4);
+    ld2<L::A13, L::B13>(row + cp, f[1], f[3]);
+    ld2<L::A56, L::B56>(row + cp, f[5], f[6]);
+    ld2<L::A78, L::B78>(row + cp, f[7], f[8]);
 }
 
 // The 9 populations of site (x, y) of a tiled buffer with `pitch` elements per row.
@@ -78,7 +131,7 @@ template <typename T>
 __device__ __forceinline__ void load_site_xy(float f[9], const T* __restrict__ g, int pitch, int x,
                                              int y)
 {
-    load_site(f, g + (size_t)y * pitch, tsingle(x), tpair(x));
+    load_site(f, g + (size_t)y * pitch, tsingle(x), tpair<T>(x));
 }
 
 // Two-belt force sums of Eq. FORCE in pair form. r[k] points at the stencil

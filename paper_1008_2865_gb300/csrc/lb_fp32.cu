@@ -90,7 +90,8 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     const int xc = wrapi(x0 - 1 + tid, nx);
     const int pc0 = wrapi(x0 - 3 + tid, nx);
     const int pc1 = wrapi(x0 - 3 + BX + (tid & 3), nx);
-    const int cs = tsingle(xc), cp = tpair(xc);   // the column's single and pair offsets
+    using TL = Tile<T>;
+    const int cs = tsingle(xc), cp = tpair<T>(xc);   // the column's single and pair offsets
     const int r0 = DIR > 0 ? y0 - 1 : y1;    // first collision row
 
     for (int rr = r0 - 2; rr <= r0 + 2; ++rr) {
@@ -166,9 +167,9 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
         const bool st_0 = out_site;
         const bool st_a = out_col && ra >= y0 && ra < y1;
         constexpr int ib = DIR > 0 ? 4 : 2, ia = DIR > 0 ? 2 : 4;   // own speeds with c_y = -DIR, +DIR
-        constexpr int ob = DIR > 0 ? kPop4 : kPop2, oa = DIR > 0 ? kPop2 : kPop4;
+        constexpr int ob = DIR > 0 ? TL::P4 : TL::P2, oa = DIR > 0 ? TL::P2 : TL::P4;
         if (st_b) st_(a.g_out + (sb + cs + ob), gs[ib]);
-        if (st_0) st_(a.g_out + (sc + cs + kPop0), gs[0]);
+        if (st_0) st_(a.g_out + (sc + cs + TL::P0), gs[0]);
         if (st_a) st_(a.g_out + (sa + cs + oa), gs[ia]);
         const float own_b = gs[ib], own_0 = gs[0], own_a = gs[ia];
         __syncthreads();
@@ -180,13 +181,13 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
         // behind row (7, 8) = (L, R) marching down, (5, 6) = (R, L) marching up;
         // row r (1, 3) = (R, L); ahead row (5, 6) = (R, L) down, (7, 8) = (L, R) up
         if (st_b) {
-            if (DIR > 0) st_pair(a.g_out + (sb + cp + kPair78), Lb, Rb);
-            else st_pair(a.g_out + (sb + cp + kPair56), Rb, Lb);
+            if (DIR > 0) st2<TL::A78, TL::B78>(a.g_out + (sb + cp), Lb, Rb);
+            else st2<TL::A56, TL::B56>(a.g_out + (sb + cp), Rb, Lb);
         }
-        if (st_0) st_pair(a.g_out + (sc + cp + kPair13), R.y, L.y);
+        if (st_0) st2<TL::A13, TL::B13>(a.g_out + (sc + cp), R.y, L.y);
         if (st_a) {
-            if (DIR > 0) st_pair(a.g_out + (sa + cp + kPair56), Ra, La);
-            else st_pair(a.g_out + (sa + cp + kPair78), La, Ra);
+            if (DIR > 0) st2<TL::A56, TL::B56>(a.g_out + (sa + cp), Ra, La);
+            else st2<TL::A78, TL::B78>(a.g_out + (sa + cp), La, Ra);
         }
         const float gb = own_b + (Rb + Lb);     // behind-group sum into row r-DIR
         const float g0 = own_0 + (R.y + L.y);   // zero-group sum of row r
@@ -340,13 +341,14 @@ __global__ void __launch_bounds__(256) k_delta_init(T* __restrict__ g, float* __
             const double d = rho[s] - rho_ref;
             const float df = (float)d;
             T* row = g + (size_t)y * pitch;
-            const int cs = tsingle(x), cp = tpair(x);
-            st_(row + cs + kPop0, w0 * df);
-            st_(row + cs + kPop2, w1 * df);
-            st_(row + cs + kPop4, w1 * df);
-            st_pair(row + cp + kPair13, w1 * df, w1 * df);
-            st_pair(row + cp + kPair56, w2 * df, w2 * df);
-            st_pair(row + cp + kPair78, w2 * df, w2 * df);
+            using TL = Tile<T>;
+            const int cs = tsingle(x), cp = tpair<T>(x);
+            st_(row + cs + TL::P0, w0 * df);
+            st_(row + cs + TL::P2, w1 * df);
+            st_(row + cs + TL::P4, w1 * df);
+            st2<TL::A13, TL::B13>(row + cp, w1 * df, w1 * df);
+            st2<TL::A56, TL::B56>(row + cp, w2 * df, w2 * df);
+            st2<TL::A78, TL::B78>(row + cp, w2 * df, w2 * df);
             dpsi[s] = cpsi * expm1f((float)(-d * inv_rho0));
         }
     }

@@ -63,23 +63,22 @@ struct Couplings {
 Couplings couplings(double G1, double G2);
 
 // Populations of an FP32 / FP16 state ("tiled" layout): rows of 32-column
-// tiles of 288 elements. A tile holds its 32 sites' populations 0, 2 and 4 as
-// three runs of 32 (elements 0-31, 32-63, 64-95, at x % 32 within each run),
-// then the pairs (1, 3), (5, 6) and (7, 8) as three runs of 32 pairs (elements
-// 96-159, 160-223, 224-287, the pair of column x % 32 at 2 (x % 32), first
-// member first). The tile of column x in row y starts at
+// tiles of 288 elements; the tile of column x in row y starts at
 //   y * g_pitch(nx) + (x / 32) * 288.
-// The pairs are the populations a thread of the fused step always writes
-// together (the two that arrive from the neighbouring columns in one row), so
-// each pair is one 8-byte (FP32) or 4-byte (FP16) access; a warp reading the
-// populations of 32 consecutive sites makes three 128-byte (FP32) and three
-// 256-byte requests from one base address. Columns past nx in the last tile
-// of a row are padding (zero, never read by a step).
+// FP32 ("paired"): a tile holds its 32 sites' populations 0, 2 and 4 as three
+// runs of 32 (elements 0-31, 32-63, 64-95, at x % 32 within each run), then the
+// pairs (1, 3), (5, 6) and (7, 8) as three runs of 32 pairs (elements 96-159,
+// 160-223, 224-287, the pair of column x % 32 at 2 (x % 32), first member
+// first). The pairs are the populations a thread of the fused step always
+// writes together (the two that arrive from the neighbouring columns in one
+// row), so each pair is one 8-byte access.
+// FP16: population i of column x at 32 i + x % 32 (nine runs of 32): paired
+// 4-byte accesses measured no faster there, and the single runs keep one
+// offset per column.
+// Columns past nx in the last tile of a row are padding (zero, never read by a
+// step).
 constexpr int kTileW = 32;
 constexpr int kTileElems = 9 * kTileW;
-// element offsets within a tile: the single runs and the pair runs
-constexpr int kPop0 = 0, kPop2 = 32, kPop4 = 64;
-constexpr int kPair13 = 96, kPair56 = 160, kPair78 = 224;
 __host__ __device__ inline int g_pitch(int nx) { return kTileElems * ((nx + kTileW - 1) / kTileW); }
 __host__ __device__ inline long long g_elems(int nx, int ny) { return (long long)ny * g_pitch(nx); }
 
