@@ -99,12 +99,8 @@ struct AdjArgs {
     const float* dpsi;        // dpsi(t)
     const float* lam_next;    // [9][N] dJ/df(t+1)
     float* lam;               // [9][N] dJ/df(t)
-    float* Qx;
-    float* Qy;
-    float* jbx;
-    float* jby;
-    float* rbar;
-    float* dpsidrho;
+    float4* site;             // per site (j-bar x, j-bar y, rho-bar so far, psi'(rho))
+    float2* Q;                // per site psi F-bar (x, y), read by pass B as a stencil
     const double* rho_target; // terminal kernel
     double* partials;
     unsigned int* counter;
@@ -293,36 +289,42 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
         const float Fbx = vbx * inv * a.inv_omega, Fby = vby * inv * a.inv_omega;
         rb -= (vbx * vx + vby * vy) * inv;
         const float dpr = __expf(-rho * a.inv_rho0) * A.inv_sqrt_rho0;
-        A.jbx[s] = vbx * inv;
-        A.jby[s] = vby * inv;
-        A.rbar[s] = rb + dpr * (-(Fbx * Sx + Fby * Sy));
-        A.dpsidrho[s] = dpr;
-        A.Qx[s] = pc * Fbx;
-        A.Qy[s] = pc * Fby;
+        A.site[s] = make_float4(vbx * inv, vby * inv, rb + dpr * (-(Fbx * Sx + Fby * Sy)), dpr);
+        A.Q[s] = make_float2(pc * Fbx, pc * Fby);
         kahan_add(f1, c1, -pc * (Fbx * Swx + Fby * Swy));
         kahan_add(f2, c2, -pc * (Fbx * Spx + Fby * Spy));
     }
     accumulate_grid2<kAdjThreads>(f1, f2, A);
 }
 
-__global__ void __launch_bounds__(kAdjThreads) k_adj_pass_b(const AdjArgs A)
+__global__ void __launch_bounds__(kAdjThreads, 5) k_adj_pass_b(const AdjArgs A)
 {
     const StepArgs<float>& a = A.a;
     const int nx = a.nx, ny = a.ny, N = (int)a.N;
     const float omc = a.omc;
     for (int s = blockIdx.x * kAdjThreads + threadIdx.x; s < N; s += gridDim.x * kAdjThreads) {
         const int y = s / nx, x = s % nx;
-        // sum_c K_c c . Q(y + c): the x part is the force stencil of Qx, the y part of Qy
+        // sum_c K_c c . Q(y + c): the x part is the force stencil of Qx, the y part of
+        // Qy (one 8-byte load per stencil site for both)
         const Nbr5 nb = nbr5(x, y, nx, ny);
-        float q[5][5];
-        const float* rows[5] = {&q[0][2], &q[1][2], &q[2][2], &q[3][2], &q[4][2]};
+        float qx[5][5], qy[5][5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                const float2 q = __ldg(A.Q + nb.yo[k] + nb.xo[m]);
+                qx[k][m] = q.x;
+                qy[k][m] = q.y;
+            }
+        }
+        const float* rx[5] = {&qx[0][2], &qx[1][2], &qx[2][2], &qx[3][2], &qx[4][2]};
+        const float* ry[5] = {&qy[0][2], &qy[1][2], &qy[2][2], &qy[3][2], &qy[4][2]};
         float sx, sy, tx, ty;
-        gather5(A.Qx, nb, q);
-        force_sums(rows, a, sx, sy);
-        gather5(A.Qy, nb, q);
-        force_sums(rows, a, tx, ty);
-        const float rb = A.rbar[s] + A.dpsidrho[s] * (sx + ty);
-        const float jbx = A.jbx[s], jby = A.jby[s];
+        force_sums(rx, a, sx, sy);
+        force_sums(ry, a, tx, ty);
+        const float4 sv = __ldg(A.site + s);
+        const float rb = sv.z + sv.w * (sx + ty);
+        const float jbx = sv.x, jby = sv.y;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int ci = cx_of(i), cj = cy_of(i);
@@ -479,12 +481,10 @@ extern "C" lb_status lb_adjoint(lb_state* s, long steps, const double* rho_targe
     A.rho_target = tgt;
     A.partials = part;
     A.counter = cnt;
-    A.Qx = scr;
-    A.Qy = scr + (size_t)N;
-    A.jbx = scr + 2 * (size_t)N;
-    A.jby = scr + 3 * (size_t)N;
-    A.rbar = scr + 4 * (size_t)N;
-    A.dpsidrho = scr + 5 * (size_t)N;
+    // the float4 array first, at the allocation's (256-byte aligned) start, then
+    // the float2 array at 16 N bytes (8-byte aligned for any N)
+    A.site = reinterpret_cast<float4*>(scr);
+    A.Q = reinterpret_cast<float2*>(scr + 4 * (size_t)N);
     float* lamA = lam;
     float* lamB = lam + 9 * (size_t)N;
     const int grid = adj_grid(N);
