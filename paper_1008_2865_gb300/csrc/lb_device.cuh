@@ -161,6 +161,48 @@ __device__ __forceinline__ void force_sums(const float* const r[5], const StepAr
          a.K5 * ((da + dd) + 2.f * (db + dc)) + 2.f * a.K8 * (e1 - e2);
 }
 
+// force_sums and, with E (a reduction step), also the Sec. 5 energy densities
+// of energy_site from the same 24 neighbour values: the energy's class sums are
+// the pair sums of the values whose differences give the force. The energies
+// are weighted by `on` (1 for an output site, 0 otherwise) instead of a branch.
+template <bool E, typename T>
+__device__ __forceinline__ void force_energy(const float* const r[5], const StepArgs<T>& a,
+                                             float& Sx, float& Sy, float on, float pc, float& es,
+                                             float& em, float& eb)
+{
+    const float *rM2 = r[0], *rM1 = r[1], *rC = r[2], *rP1 = r[3], *rP2 = r[4];
+    const float xp1 = rC[1], xm1 = rC[-1], yp1 = rP1[0], ym1 = rM1[0];        // |c|^2 = 1
+    const float pp = rP1[1], mm = rM1[-1], pm = rM1[1], mp = rP1[-1];         // |c|^2 = 2
+    const float xp2 = rC[2], xm2 = rC[-2], yp2 = rP2[0], ym2 = rM2[0];        // |c|^2 = 4
+    const float a21 = rP1[2], am2m1 = rM1[-2], b12 = rP2[1], bm1m2 = rM2[-1]; // |c|^2 = 5
+    const float cm12 = rP2[-1], c1m2 = rM2[1], dm21 = rP1[-2], d2m1 = rM1[2];
+    const float e22 = rP2[2], em2m2 = rM2[-2], f2m2 = rM2[2], fm22 = rP2[-2]; // |c|^2 = 8
+    const float d10 = xp1 - xm1, d01 = yp1 - ym1;
+    const float d11 = pp - mm, d1m = pm - mp;
+    const float d20 = xp2 - xm2, d02 = yp2 - ym2;
+    const float da = a21 - am2m1, db = b12 - bm1m2, dc = cm12 - c1m2, dd = dm21 - d2m1;
+    const float e1 = e22 - em2m2, e2 = f2m2 - fm22;
+    Sx = a.K1 * d10 + a.K2 * (d11 + d1m) + 2.f * a.K4 * d20 +
+         a.K5 * (2.f * (da - dd) + (db - dc)) + 2.f * a.K8 * (e1 + e2);
+    Sy = a.K1 * d01 + a.K2 * (d11 - d1m) + 2.f * a.K4 * d02 +
+         a.K5 * ((da + dd) + 2.f * (db + dc)) + 2.f * a.K8 * (e1 - e2);
+    if (E) {
+        const float pr = a.psi_ref;
+        const float S1 = (xp1 + xm1) + (yp1 + ym1);
+        const float S2 = (pp + mp) + (pm + mm);
+        const float S4 = (xp2 + xm2) + (yp2 + ym2);
+        const float S5 = ((a21 + dm21) + (d2m1 + am2m1)) + ((b12 + cm12) + (c1m2 + bm1m2));
+        const float S8 = (e22 + fm22) + (f2m2 + em2m2);
+        const float b1 = a.K0 * pc + a.K1 * fmaf(4.f, pr, S1) + a.K2 * fmaf(4.f, pr, S2);
+        const float b2 =
+            a.K4 * fmaf(4.f, pr, S4) + a.K5 * fmaf(8.f, pr, S5) + a.K8 * fmaf(4.f, pr, S8);
+        const float hp = 0.5f * on * pc;
+        es = fmaf(hp, b1, es);
+        em = fmaf(hp, b2, em);
+        eb = fmaf(a.half_A1 * on * pc, pc, eb);
+    }
+}
+
 // Sec. 5 pseudo-energy densities of one site with psi = psi_ref + dpsi:
 // belt 1 with the rest coupling K0, belt 2, and the bulk term A1/2 psi^2.
 template <typename T>

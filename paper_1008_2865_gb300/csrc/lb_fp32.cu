@@ -143,13 +143,13 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
 #pragma unroll
         for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
         const float pc = a.psi_ref + rows[2][0];
+        const bool out_site = out_col && r >= y0 && r < y1;
         float Sx, Sy;
-        force_sums(rows, a, Sx, Sy);
+        // the force, and on reduction steps the Sec. 5 energies of state t at (x, r)
+        force_energy<REDUCE>(rows, a, Sx, Sy, out_site ? 1.f : 0.f, pc, es, em, eb);
         float gs[9];
         const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
-
-        const bool out_site = out_col && r >= y0 && r < y1;
-        if (REDUCE && out_site) ms += d;
+        if (REDUCE) ms = fmaf(out_site ? 1.f : 0.f, d, ms);
 
         // ---- exchange post-collision values with the neighbouring columns
         exR[r & 1][tid + 1] = make_float4(gs[8], gs[1], gs[5], 0.f);
@@ -205,10 +205,7 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
         sa = step_row<DIR>(sa, P, NP);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fn[i];
-        if (REDUCE && out_site) {
-            // Sec. 5 energies of state t at (x, r); the dpsi rows r-2..r+2 stay in the
-            // ring until the next iteration overwrites slot (r + 4 DIR) & 7
-            energy_site(rows, a.psi_ref + rows[2][0], a, es, em, eb);
+        if (REDUCE) {
             if ((k & 63) == 63) {
                 eacc[0 * BX + tid] += es;
                 eacc[1 * BX + tid] += em;
