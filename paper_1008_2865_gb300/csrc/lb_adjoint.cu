@@ -61,13 +61,52 @@ __device__ __forceinline__ Nbr5 nbr5(int x, int y, int nx, int ny)
 }
 
 // The 5 x 5 neighbourhood of a periodic FP32 field: v[k][m] = field(x + m - 2, y + k - 2).
-__device__ __forceinline__ void gather5(const float* __restrict__ fld, const Nbr5& nb,
-                                        float v[5][5])
+// For a column away from the periodic x edges (2 <= x < nx - 2, `xin`) each row is
+// one pointer with immediate offsets; otherwise every column offset is wrapped.
+__device__ __forceinline__ void gather5(const float* __restrict__ fld, const Nbr5& nb, int x,
+                                        bool xin, float v[5][5])
 {
+    if (xin) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < 5; ++k) {
+            const float* r = fld + nb.yo[k] + x;
 #pragma unroll
-        for (int m = 0; m < 5; ++m) v[k][m] = __ldg(fld + nb.yo[k] + nb.xo[m]);
+            for (int m = 0; m < 5; ++m) v[k][m] = __ldg(r + (m - 2));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) v[k][m] = __ldg(fld + nb.yo[k] + nb.xo[m]);
+        }
+    }
+}
+
+// The same for the (Qx, Qy) pairs of pass B: one 8-byte load per stencil site.
+__device__ __forceinline__ void gather5x2(const float2* __restrict__ fld, const Nbr5& nb, int x,
+                                          bool xin, float vx[5][5], float vy[5][5])
+{
+    if (xin) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float2* r = fld + nb.yo[k] + x;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                const float2 q = __ldg(r + (m - 2));
+                vx[k][m] = q.x;
+                vy[k][m] = q.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                const float2 q = __ldg(fld + nb.yo[k] + nb.xo[m]);
+                vx[k][m] = q.x;
+                vy[k][m] = q.y;
+            }
+        }
     }
 }
 
@@ -208,8 +247,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_terminal(const AdjArgs A,
         const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
         const float rho = a.rho_ref + d;
         const Nbr5 nb = nbr5(x, y, nx, ny);
+        const bool xin = x >= 2 && x < nx - 2;
         float p[5][5];
-        gather5(A.dpsi, nb, p);
+        gather5(A.dpsi, nb, x, xin, p);
         const float pr = a.psi_ref;
         const float pc = pr + p[2][2];
         // class sums of psi (not deviations) around the site
@@ -257,8 +297,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
         const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
         const float rho = a.rho_ref + d;
         const Nbr5 nb = nbr5(x, y, nx, ny);
+        const bool xin = x >= 2 && x < nx - 2;
         float p[5][5];
-        gather5(A.dpsi, nb, p);
+        gather5(A.dpsi, nb, x, xin, p);
         const float* rows[5] = {&p[0][2], &p[1][2], &p[2][2], &p[3][2], &p[4][2]};
         float Swx, Swy, Spx, Spy;
         force_sums(rows, A.aw, Swx, Swy);
@@ -297,7 +338,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_pass_a(const AdjArgs A)
     accumulate_grid2<kAdjThreads>(f1, f2, A);
 }
 
-__global__ void __launch_bounds__(kAdjThreads, 5) k_adj_pass_b(const AdjArgs A)
+__global__ void __launch_bounds__(kAdjThreads) k_adj_pass_b(const AdjArgs A)
 {
     const StepArgs<float>& a = A.a;
     const int nx = a.nx, ny = a.ny, N = (int)a.N;
@@ -307,16 +348,9 @@ __global__ void __launch_bounds__(kAdjThreads, 5) k_adj_pass_b(const AdjArgs A)
         // sum_c K_c c . Q(y + c): the x part is the force stencil of Qx, the y part of
         // Qy (one 8-byte load per stencil site for both)
         const Nbr5 nb = nbr5(x, y, nx, ny);
+        const bool xin = x >= 2 && x < nx - 2;
         float qx[5][5], qy[5][5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-#pragma unroll
-            for (int m = 0; m < 5; ++m) {
-                const float2 q = __ldg(A.Q + nb.yo[k] + nb.xo[m]);
-                qx[k][m] = q.x;
-                qy[k][m] = q.y;
-            }
-        }
+        gather5x2(A.Q, nb, x, xin, qx, qy);
         const float* rx[5] = {&qx[0][2], &qx[1][2], &qx[2][2], &qx[3][2], &qx[4][2]};
         const float* ry[5] = {&qy[0][2], &qy[1][2], &qy[2][2], &qy[3][2], &qy[4][2]};
         float sx, sy, tx, ty;
