@@ -509,3 +509,21 @@ def test_allocation_failure_returns_oom_and_cleans_up():
     # the library keeps working afterwards
     rho, _, _, _, _ = _run_gpu(rho0, 5, G1=-5.0, G2=0.0, trace_every=0)
     assert np.isfinite(rho).all()
+
+
+def test_init_input_may_be_reused_at_once():
+    """lb_init has read rho_init completely when it returns (one copy into the state,
+    then a synchronisation; the initialisation itself runs on the stream): overwriting a
+    device or pinned host rho_init right after lb_init leaves the state unchanged."""
+    torch = pytest.importorskip("torch")
+    rho0 = inputs.noisy_density(300, 200, seed=23, mean=0.7, amp=0.01, mode="rel")
+    ref = _run_gpu(rho0, 20, G1=-5.0, G2=0.6, trace_every=0)
+    for where in ("cuda", "pinned"):
+        t = torch.from_numpy(rho0.copy())
+        t = t.cuda() if where == "cuda" else t.pin_memory()
+        with Lattice(t, G1=-5.0, G2=0.6, trace_every=0) as lat:
+            t.fill_(5.0)                       # at once, before any step
+            lat.step(20)
+            got = lat.fields()
+        for u, v in zip(got, ref[:3]):
+            assert np.array_equal(u, v), where
