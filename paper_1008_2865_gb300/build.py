@@ -53,8 +53,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if needed) and return the path of liblbsc.so."""
     os.makedirs(LIBDIR, exist_ok=True)
     os.makedirs(BUILDDIR, exist_ok=True)
-    headers = [os.path.join(CSRC, "lb_internal.h"), os.path.join(CSRC, "lb_device.cuh"),
-               os.path.join(INCLUDE, "lb.h")]
+    headers = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                     if f.endswith((".h", ".cuh"))) + [os.path.join(INCLUDE, "lb.h")]
     nvcc = _nvcc()
     objs = []
     jobs = []

@@ -379,45 +379,67 @@ __global__ void __launch_bounds__(256) k_delta_fields(const T* __restrict__ g, i
     }
 }
 
+// lb_energy: the Sec. 5 sums and the mass of state t. Row by row (blockIdx.y
+// strides over rows, the threads of a block over columns; a column away from
+// the periodic x edges reads its stencil rows with immediate offsets). The
+// class sums of the psi deviations (|c|^2 = 1, 2, 4, 5, 8) and the site's
+// deviation sum are FP32 sums of 4-9 FP32 values (within a few units of
+// 2^-24 of their magnitude, ~1e-9 here); the products with the couplings and
+// every accumulation are FP64.
 template <typename T>
 __global__ void __launch_bounds__(256) k_delta_energy(const T* __restrict__ g,
                                                       const float* __restrict__ dpsi,
                                                       const StepArgs<T> a, double* out4)
 {
     const int nx = a.nx, ny = a.ny;
-    const long long N = a.N;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const double pr = a.psi_ref;
-    for (long long s = blockIdx.x * 256LL + threadIdx.x; s < N; s += (long long)gridDim.x * 256) {
-        const int y = (int)(s / nx), x = (int)(s % nx);
-        auto P = [&](int dx, int dy) -> double {
-            return (double)dpsi[(long long)wrapi(y + dy, ny) * nx + wrapi(x + dx, nx)];
-        };
-        const double pc = pr + P(0, 0);
-        const double S1 = P(1, 0) + P(-1, 0) + P(0, 1) + P(0, -1);
-        const double S2 = P(1, 1) + P(-1, 1) + P(1, -1) + P(-1, -1);
-        const double S4 = P(2, 0) + P(-2, 0) + P(0, 2) + P(0, -2);
-        const double S5 = P(2, 1) + P(-2, 1) + P(2, -1) + P(-2, -1) + P(1, 2) + P(-1, 2) +
-                          P(1, -2) + P(-1, -2);
-        const double S8 = P(2, 2) + P(-2, 2) + P(2, -2) + P(-2, -2);
-        const double b1 = (double)a.K0 * pc + (double)a.K1 * (4 * pr + S1) + (double)a.K2 * (4 * pr + S2);
-        const double b2 = (double)a.K4 * (4 * pr + S4) + (double)a.K5 * (8 * pr + S5) +
-                          (double)a.K8 * (4 * pr + S8);
-        v[0] += 0.5 * pc * b1;
-        v[1] += 0.5 * pc * b2;
-        v[2] += (double)a.half_A1 * pc * pc;
-        float f[9];
-        load_site_xy(f, g, a.pitch, x, y);
-        double d = 0.0;
+    const double K0 = a.K0, K1 = a.K1, K2 = a.K2, K4 = a.K4, K5 = a.K5, K8 = a.K8;
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        const float* rw[5];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) d += (double)f[i];
-        v[3] += d;
+        for (int k = 0; k < 5; ++k) rw[k] = dpsi + (size_t)wrapi(y + k - 2, ny) * nx;
+        for (int x = blockIdx.x * 256 + threadIdx.x; x < nx; x += gridDim.x * 256) {
+            float q[5][5];          // q[k][m] = dpsi(x + m - 2, y + k - 2)
+            if (x >= 2 && x < nx - 2) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+#pragma unroll
+                    for (int m = 0; m < 5; ++m) q[k][m] = __ldg(rw[k] + x + m - 2);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < 5; ++m) {
+                    const int xx = wrapi(x + m - 2, nx);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) q[k][m] = __ldg(rw[k] + xx);
+                }
+            }
+            const float S1 = (q[2][3] + q[2][1]) + (q[3][2] + q[1][2]);
+            const float S2 = (q[3][3] + q[3][1]) + (q[1][3] + q[1][1]);
+            const float S4 = (q[2][4] + q[2][0]) + (q[4][2] + q[0][2]);
+            const float S5 = ((q[3][4] + q[3][0]) + (q[1][4] + q[1][0])) +
+                             ((q[4][3] + q[4][1]) + (q[0][3] + q[0][1]));
+            const float S8 = (q[4][4] + q[4][0]) + (q[0][4] + q[0][0]);
+            const double pc = pr + (double)q[2][2];
+            const double b1 = K0 * pc + K1 * (4 * pr + (double)S1) + K2 * (4 * pr + (double)S2);
+            const double b2 =
+                K4 * (4 * pr + (double)S4) + K5 * (8 * pr + (double)S5) + K8 * (4 * pr + (double)S8);
+            v[0] += 0.5 * pc * b1;
+            v[1] += 0.5 * pc * b2;
+            v[2] += (double)a.half_A1 * pc * pc;
+            float f[9];
+            load_site_xy(f, g, a.pitch, x, y);
+            const float d =
+                ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+            v[3] += (double)d;
+        }
     }
-    if (last_block_total<256>(v, a.partials, a.counter, gridDim.x)) {
+    if (last_block_total<256>(v, a.partials, a.counter, gridDim.x * gridDim.y)) {
         out4[0] = v[0];
         out4[1] = v[1];
         out4[2] = v[2];
-        out4[3] = (double)N * (double)a.rho_ref + v[3];
+        out4[3] = (double)a.N * (double)a.rho_ref + v[3];
     }
 }
 
@@ -573,7 +595,12 @@ cudaError_t delta_energy(const T* g, const float* dpsi, int nx, int ny, const St
     StepArgs<T> b = a;
     b.partials = partials;
     b.counter = counter;
-    k_delta_energy<T><<<helper_grid((long long)nx * ny), 256, 0, s>>>(g, dpsi, b, out4);
+    // at most 152 x 16 CTAs (the state's partial buffer holds at least that many)
+    int bx = (nx + 255) / 256;
+    if (bx > 32) bx = 32;
+    int by = 152 * 16 / bx;
+    if (by > ny) by = ny;
+    k_delta_energy<T><<<dim3(bx, by), 256, 0, s>>>(g, dpsi, b, out4);
     return cudaGetLastError();
 }
 
