@@ -21,6 +21,7 @@ struct lb_batch {
     int block_x = 128, rows = 32;
     bool use_graph = true;
     bool om1 = true;
+    bool alternate = false;   // some replica marches in alternating directions
     int num_sms = 1;
     long long t = 0;
     int cur = 0;
@@ -90,7 +91,8 @@ lb_status build_tables(lb_batch* b)
         ri.err = s->err;
         info.push_back(ri);
         for (int by = 0; by < nty; ++by)
-            for (int bx = 0; bx < ntx; ++bx) tiles.push_back(make_int4((int)r, bx, by, 0));
+            for (int bx = 0; bx < ntx; ++bx)
+                tiles.push_back(make_int4((int)r, bx, by, marches_alternate(s->N) ? 1 : 0));
     }
     b->ntiles = (int)tiles.size();
     const bool ok =
@@ -117,12 +119,12 @@ cudaError_t enqueue_step(const lb_batch* b, cudaStream_t s, long long t, int cur
     if (b->prec == LB_FP32) {
         BatchLaunch<float> L{static_cast<const StepArgs<float>*>(b->d_args[cur]), b->d_tiles,
                              b->ntiles, b->d_partials, b->d_reps, (int)b->reps.size(),
-                             b->block_x, b->om1, b->trace_every, b->num_sms};
+                             b->block_x, b->om1, b->trace_every, b->num_sms, b->alternate};
         return fp32_batch_step(L, reduce, s);
     }
     BatchLaunch<__half> L{static_cast<const StepArgs<__half>*>(b->d_args[cur]), b->d_tiles,
                           b->ntiles, b->d_partials, b->d_reps, (int)b->reps.size(),
-                          b->block_x, b->om1, b->trace_every, b->num_sms};
+                          b->block_x, b->om1, b->trace_every, b->num_sms, b->alternate};
     return fp16_batch_step(L, reduce, s);
 }
 
@@ -196,6 +198,7 @@ lb_status lb_batch_init(lb_batch** out, int count, const lb_params* params,
         }
         b->reps.push_back(s);
         b->om1 = b->om1 && params[r].omega == 1.0;
+        b->alternate = b->alternate || marches_alternate(s->N);
     }
     DeviceScope dev(b->device);
     if (!dev.ok ||

@@ -161,10 +161,13 @@ __device__ __forceinline__ void force_sums(const float* const r[5], const StepAr
          a.K5 * ((da + dd) + 2.f * (db + dc)) + 2.f * a.K8 * (e1 - e2);
 }
 
-// force_sums and, with E (a reduction step), also the Sec. 5 energy densities
-// of energy_site from the same 24 neighbour values: the energy's class sums are
-// the pair sums of the values whose differences give the force. The energies
-// are weighted by `on` (1 for an output site, 0 otherwise) instead of a branch.
+// force_sums and, with E (a reduction step), also the Sec. 5 energies from the
+// same neighbour values. Only lattice totals of the energies are wanted, and on
+// the periodic lattice sum_x psi(x) psi(x + c) = sum_x psi(x) psi(x - c)
+// (translate x by c), so each class sum takes one member of every pair
+// (c, -c), doubled: the totals equal those of energy_site's full class sums,
+// the per-site terms do not. The energies are weighted by `on` (1 for an
+// output site, 0 otherwise) instead of a branch.
 template <bool E, typename T>
 __device__ __forceinline__ void force_energy(const float* const r[5], const StepArgs<T>& a,
                                              float& Sx, float& Sy, float on, float pc, float& es,
@@ -188,14 +191,14 @@ __device__ __forceinline__ void force_energy(const float* const r[5], const Step
          a.K5 * ((da + dd) + 2.f * (db + dc)) + 2.f * a.K8 * (e1 - e2);
     if (E) {
         const float pr = a.psi_ref;
-        const float S1 = (xp1 + xm1) + (yp1 + ym1);
-        const float S2 = (pp + mp) + (pm + mm);
-        const float S4 = (xp2 + xm2) + (yp2 + ym2);
-        const float S5 = ((a21 + dm21) + (d2m1 + am2m1)) + ((b12 + cm12) + (c1m2 + bm1m2));
-        const float S8 = (e22 + fm22) + (f2m2 + em2m2);
-        const float b1 = a.K0 * pc + a.K1 * fmaf(4.f, pr, S1) + a.K2 * fmaf(4.f, pr, S2);
-        const float b2 =
-            a.K4 * fmaf(4.f, pr, S4) + a.K5 * fmaf(8.f, pr, S5) + a.K8 * fmaf(4.f, pr, S8);
+        const float H1 = xp1 + yp1;                        // (1,0), (0,1)
+        const float H2 = pp + pm;                          // (1,1), (1,-1)
+        const float H4 = xp2 + yp2;                        // (2,0), (0,2)
+        const float H5 = (a21 + b12) + (cm12 + dm21);      // (2,1), (1,2), (-1,2), (-2,1)
+        const float H8 = e22 + f2m2;                       // (2,2), (2,-2)
+        const float b1 = a.K0 * pc + a.K1 * fmaf(2.f, H1, 4.f * pr) + a.K2 * fmaf(2.f, H2, 4.f * pr);
+        const float b2 = a.K4 * fmaf(2.f, H4, 4.f * pr) + a.K5 * fmaf(2.f, H5, 8.f * pr) +
+                         a.K8 * fmaf(2.f, H8, 4.f * pr);
         const float hp = 0.5f * on * pc;
         es = fmaf(hp, b1, es);
         em = fmaf(hp, b2, em);

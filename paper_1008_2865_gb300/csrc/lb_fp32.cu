@@ -11,7 +11,7 @@
 // Work decomposition. A CTA of BX threads owns a strip of BX-2 output
 // columns and `rows` output rows; thread k sits on column x0-1+k, so the two
 // edge threads are the one-column halo whose collisions the interior needs.
-// The CTA marches over its rows; on lattices larger than L2, plain steps march
+// The CTA marches over its rows; on lattices larger than L2, the steps march
 // down in even row chunks and up in odd ones (so that the two CTAs reading a
 // chunk boundary's halo row read it at about the same time, and the second
 // read hits L2). For collision row r it
@@ -73,7 +73,7 @@ __device__ __forceinline__ int step_row(int off, int stride, int total)
 // row reach it at about the same time and the second read hits L2. With
 // REDUCE, v receives this thread's FP64 partial sums {E_s, E_m, E_bulk, sum of
 // rho - rho_ref} of state t over its sites.
-template <typename T, int BX, bool REDUCE, bool OM1, int DIR>
+template <typename T, int BX, bool REDUCE, bool OM1, bool MIRROR, int DIR>
 __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int by, double v[4],
                                               float (*win)[BX + 4], float4 (*exR)[BX + 2],
                                               float4 (*exL)[BX + 2], double* eacc)
@@ -95,10 +95,20 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     const int cs = tsingle(xc), cp = tpair<T>(xc);   // the column's single and pair offsets
     const int r0 = DIR > 0 ? y0 - 1 : y1;    // first collision row
 
+    // ring slot q = row & 7 of dpsi row `row`; with MIRROR, slots 0..3 are
+    // repeated in 8..11, so that the five rows r-2 .. r+2 sit in consecutive slots
+    // from (r-2) & 7 and one base address serves the whole stencil
     for (int rr = r0 - 2; rr <= r0 + 2; ++rr) {
         const float* src = a.dpsi_in + wrapi(rr, ny) * nx;
-        win[rr & 7][tid] = __ldg(src + pc0);
-        if (tid < 4) win[rr & 7][BX + tid] = __ldg(src + pc1);
+        const float v0 = __ldg(src + pc0);
+        const float v1 = tid < 4 ? __ldg(src + pc1) : 0.f;
+        const int q = rr & 7;
+        win[q][tid] = v0;
+        if (tid < 4) win[q][BX + tid] = v1;
+        if (MIRROR && q < 4) {
+            win[q + 8][tid] = v0;
+            if (tid < 4) win[q + 8][BX + tid] = v1;
+        }
     }
     // Row offsets (row * P) of g, periodic, kept incrementally: at the top of
     // iteration r, sb, sc, sa hold rows r-DIR (behind), r, r+DIR (ahead) and oq
@@ -142,9 +152,10 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
         // ---- force from the dpsi(t) ring, then moments and collision
         const float* rows[5];
 #pragma unroll
-        for (int j = 0; j < 5; ++j) rows[j] = &win[(r - 2 + j) & 7][tid + 2];
+        for (int j = 0; j < 5; ++j)
+            rows[j] = MIRROR ? &win[((r - 2) & 7) + j][tid + 2] : &win[(r - 2 + j) & 7][tid + 2];
         const float pc = a.psi_ref + rows[2][0];
-        const bool out_site = out_col && r >= y0 && r < y1;
+        const bool out_site = out_col && k >= 1 && k <= nrows;
         float Sx, Sy;
         // the force, and on reduction steps the Sec. 5 energies of state t at (x, r)
         force_energy<REDUCE>(rows, a, Sx, Sy, out_site ? 1.f : 0.f, pc, es, em, eb);
@@ -156,17 +167,23 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
         exR[r & 1][tid + 1] = make_float4(gs[8], gs[1], gs[5], 0.f);
         exL[r & 1][tid + 1] = make_float4(gs[7], gs[3], gs[6], 0.f);
         if (more) {
-            win[(r + 3 * DIR) & 7][tid] = pn0;
-            if (tid < 4) win[(r + 3 * DIR) & 7][BX + tid] = pn1;
+            const int q = (r + 3 * DIR) & 7;
+            win[q][tid] = pn0;
+            if (tid < 4) win[q][BX + tid] = pn1;
+            if (MIRROR && q < 4) {
+                win[q + 8][tid] = pn0;
+                if (tid < 4) win[q + 8][BX + tid] = pn1;
+            }
         }
         // ---- f(t+1) = f*(x - c_i) (Eq. 1) for the own column: the speeds with
         // c_y = -DIR land in the behind row, c_y = 0 in row r, c_y = +DIR in the
         // ahead row. The own-column speeds are stored now, the six from the
         // neighbouring columns after the barrier.
-        const int rb = r - DIR, ra = r + DIR;
-        const bool st_b = out_col && rb >= y0 && rb < y1;
+        const int rb = r - DIR;
+        // rows r - DIR, r, r + DIR are output rows for k >= 2, 1 <= k <= nrows, k < nrows
+        const bool st_b = out_col && k >= 2;
         const bool st_0 = out_site;
-        const bool st_a = out_col && ra >= y0 && ra < y1;
+        const bool st_a = out_col && k < nrows;
         constexpr int ib = DIR > 0 ? 4 : 2, ia = DIR > 0 ? 2 : 4;   // own speeds with c_y = -DIR, +DIR
         constexpr int ob = DIR > 0 ? TL::P4 : TL::P2, oa = DIR > 0 ? TL::P2 : TL::P4;
         if (st_b) st_(a.g_out + (sb + cs + ob), gs[ib]);
@@ -225,24 +242,27 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     }
 }
 
-// The tile of chunk `by`. With ALTERNATE and `alternate` (the launcher sets it
-// for states larger than L2), plain steps march down in even chunks and up in
-// odd ones; reduction steps, and every tile of a batch, march down. Fields do not depend on the direction (each site's arithmetic, and the
-// order of the rho(t+1) sum, are the same either way); the per-thread energy
-// and mass sums do, so keeping the reduction steps on one direction keeps a
-// batch replica's trace bit-identical to the same lattice run alone.
-template <typename T, int BX, bool REDUCE, bool OM1, bool ALTERNATE>
+// The tile of chunk `by`. With ALTERNATE and `alternate` (marches_alternate:
+// states larger than L2), the tile marches down in even chunks and up in odd
+// ones, otherwise down. Fields do not depend on the direction (each site's
+// arithmetic, and the order of the rho(t+1) sum, are the same either way); the
+// per-thread energy and mass sums of a reduction step do, so a batch replica
+// takes the direction its lattice takes alone, and its trace stays
+// bit-identical to that run's. MIRROR: the ring's stencil rows from one base
+// address (single-lattice plain steps; the reduction and batch kernels keep
+// the 8-slot ring, measured faster there).
+template <typename T, int BX, bool REDUCE, bool OM1, bool ALTERNATE, bool MIRROR>
 __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, double v[4],
                                           bool alternate = true)
 {
-    __shared__ float win[8][BX + 4];          // dpsi(t) rows, slot = row & 7
+    __shared__ float win[MIRROR ? 12 : 8][BX + 4];   // dpsi(t) rows, slot = row & 7
     __shared__ float4 exR[2][BX + 2];        // right-moving f*: speeds 8, 1, 5 (cy = -1, 0, +1)
     __shared__ float4 exL[2][BX + 2];        // left-moving f*: speeds 7, 3, 6
     __shared__ double eacc[REDUCE ? 4 * BX : 1];   // FP64 energy/mass slots of the threads
-    if (ALTERNATE && !REDUCE && alternate && (by & 1))
-        step_tile_dir<T, BX, REDUCE, OM1, -1>(a, bx, by, v, win, exR, exL, eacc);
+    if (ALTERNATE && alternate && (by & 1))
+        step_tile_dir<T, BX, REDUCE, OM1, MIRROR, -1>(a, bx, by, v, win, exR, exL, eacc);
     else
-        step_tile_dir<T, BX, REDUCE, OM1, +1>(a, bx, by, v, win, exR, exL, eacc);
+        step_tile_dir<T, BX, REDUCE, OM1, MIRROR, +1>(a, bx, by, v, win, exR, exL, eacc);
 }
 
 template <typename T, int BX, bool REDUCE, bool OM1>
@@ -250,7 +270,7 @@ __global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / B
     k_step(const StepArgs<T> a, bool alternate)
 {
     double v[4];
-    step_tile<T, BX, REDUCE, OM1, true>(a, blockIdx.x, blockIdx.y, v, alternate);
+    step_tile<T, BX, REDUCE, OM1, true, !REDUCE>(a, blockIdx.x, blockIdx.y, v, alternate);
     if (REDUCE) {
         const unsigned int nb = gridDim.x * gridDim.y;
         if (last_block_total<BX>(v, a.partials, a.counter, nb)) {
@@ -266,26 +286,28 @@ __global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / B
 // one launch: a persistent grid strides over a work list of tiles, each tile
 // = (replica, strip, row chunk) of that replica's own launch shape, and runs
 // exactly the per-tile code of k_step. The replica's arguments are staged in
-// shared memory once per tile. Tiles march down. With REDUCE each tile's CTA
-// partial (the same block sum k_step forms) goes to tile_partials;
-// k_batch_reduce then sums a replica's partials in the order k_step's last CTA
-// uses, so a replica's fields and trace are bit-identical to running it alone
-// with the same shape. (Measured on the 96-replica sweep and not kept: tiles
-// handed out by an atomic counter, 1.2% slower; alternating march directions,
-// no gain and more registers than the 40-warp budget allows.)
-template <typename T, int BX, bool REDUCE, bool OM1>
-__global__ void __launch_bounds__(BX, (REDUCE ? 28 : 40) * 32 / BX)
+// shared memory once per tile. A tile marches as k_step marches it (tl.w: the
+// replica alternates; ALTERNATE: some replica does, and its kernels get a
+// 36-warp register budget). With REDUCE each tile's CTA partial (the same block
+// sum k_step forms) goes to tile_partials; k_batch_reduce then sums a
+// replica's partials in the order k_step's last CTA uses, so a replica's
+// fields and trace are bit-identical to running it alone with the same shape.
+// (Measured on the 96-replica sweep and not kept: tiles handed out by an
+// atomic counter, 1.2% slower; alternating march directions for replicas that
+// fit in L2, no gain.)
+template <typename T, int BX, bool REDUCE, bool OM1, bool ALTERNATE>
+__global__ void __launch_bounds__(BX, (REDUCE ? 28 : ALTERNATE ? 36 : 40) * 32 / BX)
     k_step_batch(const StepArgs<T>* __restrict__ args, const int4* __restrict__ tiles, int ntiles,
                  double* __restrict__ tile_partials)
 {
     __shared__ StepArgs<T> sa;
     for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
-        const int4 tl = tiles[k];                   // (replica, strip, chunk, -)
+        const int4 tl = tiles[k];                   // (replica, strip, chunk, alternate)
         __syncthreads();                            // previous tile done with sa and smem rings
         if (threadIdx.x == 0) sa = args[tl.x];
         __syncthreads();
         double v[4];
-        step_tile<T, BX, REDUCE, OM1, false>(sa, tl.y, tl.z, v);
+        step_tile<T, BX, REDUCE, OM1, ALTERNATE, false>(sa, tl.y, tl.z, v, tl.w != 0);
         if (REDUCE) {
             block_sum4<BX>(v);
             if (threadIdx.x == 0) {
@@ -463,12 +485,10 @@ cudaError_t launch_step_bx(const StepArgs<T>& a, Fp32Launch L, bool reduce, cuda
 {
     dim3 grid((a.nx + BX - 3) / (BX - 2), (a.ny + L.rows - 1) / L.rows);
     const bool om1 = a.omega == 1.0f;
-    // Alternating march directions only pay when the state does not fit in L2
-    // (measured: 2% slower at 1024^2, faster from 2048^2 on).
-    const bool alt = (long long)a.N * 80 > (128LL << 20);
+    const bool alt = marches_alternate(a.N);
     if (reduce) {
-        if (om1) k_step<T, BX, true, true><<<grid, BX, 0, s>>>(a, false);
-        else k_step<T, BX, true, false><<<grid, BX, 0, s>>>(a, false);
+        if (om1) k_step<T, BX, true, true><<<grid, BX, 0, s>>>(a, alt);
+        else k_step<T, BX, true, false><<<grid, BX, 0, s>>>(a, alt);
     } else {
         if (om1) k_step<T, BX, false, true><<<grid, BX, 0, s>>>(a, alt);
         else k_step<T, BX, false, false><<<grid, BX, 0, s>>>(a, alt);
@@ -522,10 +542,21 @@ cudaError_t launch_batch_bx(const BatchLaunch<T>& b, bool reduce, cudaStream_t s
         return cudaGetLastError();
     };
     cudaError_t e;
-    if (reduce)
-        e = b.om1 ? pick(k_step_batch<T, BX, true, true>) : pick(k_step_batch<T, BX, true, false>);
-    else
-        e = b.om1 ? pick(k_step_batch<T, BX, false, true>) : pick(k_step_batch<T, BX, false, false>);
+    if (b.alternate) {
+        if (reduce)
+            e = b.om1 ? pick(k_step_batch<T, BX, true, true, true>)
+                      : pick(k_step_batch<T, BX, true, false, true>);
+        else
+            e = b.om1 ? pick(k_step_batch<T, BX, false, true, true>)
+                      : pick(k_step_batch<T, BX, false, false, true>);
+    } else {
+        if (reduce)
+            e = b.om1 ? pick(k_step_batch<T, BX, true, true, false>)
+                      : pick(k_step_batch<T, BX, true, false, false>);
+        else
+            e = b.om1 ? pick(k_step_batch<T, BX, false, true, false>)
+                      : pick(k_step_batch<T, BX, false, false, false>);
+    }
     if (e != cudaSuccess || !reduce) return e;
     k_batch_reduce<BX><<<b.nreps, BX, 0, s>>>(b.tile_partials, b.reps, b.trace_every);
     return cudaGetLastError();
