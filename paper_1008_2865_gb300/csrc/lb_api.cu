@@ -325,6 +325,9 @@ lb_status lb_init(lb_state** out, const lb_params* p, const double* rho_init, vo
         (size_t)bulk_grid_blocks(p->nx, p->ny, (int)elem_size(p->prec), Fp32Launch{64, kMinRows, 1});
     if (nblk_bulk > nblk_step) nblk_step = nblk_bulk;
     s->partials_cap = nblk_step > 152 * 16 ? nblk_step : 152 * 16;
+    // the reduction step's grid sum keeps one total per CTA row after the CTA partials
+    s->max_cta_rows = (p->ny + kMinRows - 1) / kMinRows;
+    s->partials_cap += (size_t)s->max_cta_rows;
     bool ok = alloc((void**)&s->partials, 4 * sizeof(double) * s->partials_cap) &&
               alloc((void**)&s->counter, sizeof(unsigned int)) &&
               alloc((void**)&s->trace, sizeof(double) * kTraceCap * kTraceCols) &&
@@ -729,7 +732,8 @@ lb_status lb_set_launch(lb_state* s, int block_x, int rows_per_cta, int pipeline
     }
     const Fp32Launch L{block_x, rows_per_cta, pipeline};
     // the CTA-partial buffer was sized for the smallest CTAs (64 threads, kMinRows rows)
-    if (step_blocks(s, L) > s->partials_cap) return LB_ERR_ARG;
+    // and one row total per CTA row
+    if (step_blocks(s, L) + (size_t)s->max_cta_rows > s->partials_cap) return LB_ERR_ARG;
     s->launch = L;
     return LB_OK;
 }

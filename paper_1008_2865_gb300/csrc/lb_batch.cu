@@ -30,6 +30,8 @@ struct lb_batch {
     void* d_args[2] = {nullptr, nullptr};   // StepArgs<T>[nreps] for buffers 0 and 1
     int4* d_tiles = nullptr;
     int ntiles = 0;
+    int2* d_rowmap = nullptr;   // (replica, row chunk) of each grid-sum CTA
+    int nrows = 0;
     double* d_partials = nullptr;
     BatchRep* d_reps = nullptr;
     // graph of one period of steps, starting at t % period == 0
@@ -42,11 +44,13 @@ namespace {
 
 void free_tables(lb_batch* b)
 {
-    void* ptrs[] = {b->d_args[0], b->d_args[1], b->d_tiles, b->d_partials, b->d_reps};
+    void* ptrs[] = {b->d_args[0], b->d_args[1], b->d_tiles, b->d_partials, b->d_reps,
+                    b->d_rowmap};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     b->d_args[0] = b->d_args[1] = nullptr;
     b->d_tiles = nullptr;
+    b->d_rowmap = nullptr;
     b->d_partials = nullptr;
     b->d_reps = nullptr;
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -77,6 +81,8 @@ lb_status build_tables(lb_batch* b)
     free_tables(b);
     std::vector<int4> tiles;
     std::vector<BatchRep> info;
+    std::vector<int2> rowmap;
+    int nrows_total = 0;
     for (size_t r = 0; r < b->reps.size(); ++r) {
         const lb_state* s = b->reps[r];
         const int ntx = (s->p.nx + b->block_x - 3) / (b->block_x - 2);
@@ -84,6 +90,11 @@ lb_status build_tables(lb_batch* b)
         BatchRep ri;
         ri.first_tile = (int)tiles.size();
         ri.ntiles = ntx * nty;
+        ri.ntx = ntx;
+        ri.first_row = nrows_total;   // offset by the tile count below
+        ri.counter = s->counter;
+        for (int y = 0; y < nty; ++y) rowmap.push_back(make_int2((int)r, y));
+        nrows_total += nty;
         ri.N = s->N;
         ri.rho_ref = s->rho_ref;
         ri.trace = s->trace;
@@ -95,12 +106,18 @@ lb_status build_tables(lb_batch* b)
                 tiles.push_back(make_int4((int)r, bx, by, marches_alternate(s->N) ? 1 : 0));
     }
     b->ntiles = (int)tiles.size();
+    b->nrows = nrows_total;
+    for (BatchRep& ri : info) ri.first_row += b->ntiles;
     const bool ok =
         (b->prec == LB_FP32 ? upload_args<float>(b) : upload_args<__half>(b)) &&
         cudaMalloc((void**)&b->d_tiles, sizeof(int4) * tiles.size()) == cudaSuccess &&
         cudaMemcpy(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(),
                    cudaMemcpyHostToDevice) == cudaSuccess &&
-        cudaMalloc((void**)&b->d_partials, 4 * sizeof(double) * tiles.size()) == cudaSuccess &&
+        cudaMalloc((void**)&b->d_partials, 4 * sizeof(double) * (tiles.size() + nrows_total)) ==
+            cudaSuccess &&
+        cudaMalloc((void**)&b->d_rowmap, sizeof(int2) * rowmap.size()) == cudaSuccess &&
+        cudaMemcpy(b->d_rowmap, rowmap.data(), sizeof(int2) * rowmap.size(),
+                   cudaMemcpyHostToDevice) == cudaSuccess &&
         cudaMalloc((void**)&b->d_reps, sizeof(BatchRep) * info.size()) == cudaSuccess &&
         cudaMemcpy(b->d_reps, info.data(), sizeof(BatchRep) * info.size(),
                    cudaMemcpyHostToDevice) == cudaSuccess;
@@ -119,12 +136,14 @@ cudaError_t enqueue_step(const lb_batch* b, cudaStream_t s, long long t, int cur
     if (b->prec == LB_FP32) {
         BatchLaunch<float> L{static_cast<const StepArgs<float>*>(b->d_args[cur]), b->d_tiles,
                              b->ntiles, b->d_partials, b->d_reps, (int)b->reps.size(),
-                             b->block_x, b->om1, b->trace_every, b->num_sms, b->alternate};
+                             b->d_rowmap, b->nrows, b->block_x, b->om1, b->trace_every,
+                             b->num_sms, b->alternate};
         return fp32_batch_step(L, reduce, s);
     }
     BatchLaunch<__half> L{static_cast<const StepArgs<__half>*>(b->d_args[cur]), b->d_tiles,
                           b->ntiles, b->d_partials, b->d_reps, (int)b->reps.size(),
-                          b->block_x, b->om1, b->trace_every, b->num_sms, b->alternate};
+                          b->d_rowmap, b->nrows, b->block_x, b->om1, b->trace_every,
+                          b->num_sms, b->alternate};
     return fp16_batch_step(L, reduce, s);
 }
 

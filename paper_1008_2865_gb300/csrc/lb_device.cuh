@@ -291,20 +291,22 @@ __device__ __forceinline__ float dpsi_of(float d, const StepArgs<T>& a)
 // in shared memory and warp 0 alone does the FP64 adds (fixed strided order,
 // then a fixed shuffle tree): FP64 issues slowly on this part, so the adds of
 // one warp instead of every warp's shuffle tree.
+// `red` is 4 NT doubles of shared memory (k-major); each thread writes only its
+// own slots before the first barrier, so a buffer whose slot (k, tid) the
+// thread itself last used may serve.
 template <int NT>
-__device__ void block_sum4(double v[4])
+__device__ void block_sum4(double v[4], double* red)
 {
-    __shared__ double red[4][NT];
     const int tid = threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) red[k][tid] = v[k];
+    for (int k = 0; k < 4; ++k) red[k * NT + tid] = v[k];
     __syncthreads();
     if (tid < 32) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            double w = red[k][tid];
+            double w = red[k * NT + tid];
 #pragma unroll
-            for (int j = tid + 32; j < NT; j += 32) w += red[k][j];
+            for (int j = tid + 32; j < NT; j += 32) w += red[k * NT + j];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
             v[k] = w;
@@ -312,41 +314,34 @@ __device__ void block_sum4(double v[4])
     }
     __syncthreads();
 }
-
-// Store this CTA's partial, and if it is the last CTA to arrive, sum all
-// partials (each thread a fixed strided subset, then a fixed tree) and return
-// true in thread 0 with the total in v. Resets the counter for the next use.
 template <int NT>
-__device__ bool last_block_total(double v[4], double* partials, unsigned int* counter,
-                                 unsigned int nblocks)
+__device__ void block_sum4(double v[4])
 {
-    __shared__ bool s_last;
-    const unsigned int b = blockIdx.y * gridDim.x + blockIdx.x;
-    block_sum4<NT>(v);
-    if (threadIdx.x == 0) {
+    __shared__ double red[4 * NT];
+    block_sum4<NT>(v, red);
+}
+
+// Sum of n 4-double partials p[0..n) over a CTA of NT threads: thread k adds
+// partials k, k + NT, k + 2 NT, ... in that order, then block_sum4's tree; the
+// total is valid in thread 0. The loads of U partials are issued together
+// (one L2 round trip instead of U); U does not change the order of the adds.
+template <int NT, int U = 4>
+__device__ void sum_partials(const double* partials, unsigned int nblocks, double w[4],
+                             double* red)
+{
 #pragma unroll
-        for (int k = 0; k < 4; ++k) partials[4 * (size_t)b + k] = v[k];
-        __threadfence();
-        const unsigned int prev = atomicAdd(counter, 1u);
-        s_last = (prev == nblocks - 1);
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    double w[4] = {0.0, 0.0, 0.0, 0.0};
-    // thread k adds partials k, k + NT, k + 2 NT, ... in that order; the loads of
-    // four of them are issued together (one L2 round trip instead of four)
+    for (int k = 0; k < 4; ++k) w[k] = 0.0;
     unsigned int j = threadIdx.x;
-    for (; j + 3 * NT < nblocks; j += 4 * NT) {
-        double2 q[4][2];
+    for (; j + (U - 1) * NT < nblocks; j += U * NT) {
+        double2 q[U][2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             const double2* p2 = reinterpret_cast<const double2*>(partials + 4 * (size_t)(j + u * NT));
             q[u][0] = __ldcg(p2);
             q[u][1] = __ldcg(p2 + 1);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             w[0] += q[u][0].x;
             w[1] += q[u][0].y;
             w[2] += q[u][1].x;
@@ -357,12 +352,70 @@ __device__ bool last_block_total(double v[4], double* partials, unsigned int* co
 #pragma unroll
         for (int k = 0; k < 4; ++k) w[k] += __ldcg(partials + 4 * (size_t)j + k);
     }
-    block_sum4<NT>(w);
+    block_sum4<NT>(w, red);
+}
+
+// Store this CTA's partial, and if it is the last CTA to arrive, sum all
+// partials (sum_partials) and return true in thread 0 with the total in v.
+// Resets the counter for the next use. `red`: the block sums' shared buffer
+// (4 NT doubles, as block_sum4).
+template <int NT>
+__device__ bool last_block_total(double v[4], double* partials, unsigned int* counter,
+                                 unsigned int nblocks, double* red)
+{
+    __shared__ bool s_last;
+    const unsigned int b = blockIdx.y * gridDim.x + blockIdx.x;
+    block_sum4<NT>(v, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) partials[4 * (size_t)b + k] = v[k];
+        __threadfence();
+        const unsigned int prev = atomicAdd(counter, 1u);
+        s_last = (prev == nblocks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double w[4];
+    sum_partials<NT>(partials, nblocks, w, red);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = w[k];
         *counter = 0u;
     }
+    return threadIdx.x == 0;
+}
+template <int NT>
+__device__ bool last_block_total(double v[4], double* partials, unsigned int* counter,
+                                 unsigned int nblocks)
+{
+    __shared__ double red[4 * NT];
+    return last_block_total<NT>(v, partials, counter, nblocks, red);
+}
+
+// Grid sum of a reduction step in two levels, so that the FP64 adds (a slow
+// pipe on this part) spread over many SMs instead of the one last CTA: CTA row
+// y of the step's grid left its nbx partials at cta[y nbx .. y nbx + nbx); one
+// CTA per row sums them (sum_partials) into rows[y], and the last row of the
+// lattice to finish (arrival counter, reset here) sums rows[0 .. nby) the same
+// way. Returns true in thread 0 of that CTA, with the total in w.
+template <int NT>
+__device__ bool row_then_total(const double* cta, int nbx, int nby, int y, double* rows,
+                               unsigned int* counter, double w[4], double* red)
+{
+    __shared__ bool s_last;
+    sum_partials<NT, 1>(cta + 4 * (size_t)y * nbx, nbx, w, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rows[4 * (size_t)y + k] = w[k];
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == (unsigned int)nby - 1;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    sum_partials<NT, 1>(rows, nby, w, red);
+    if (threadIdx.x == 0) *counter = 0u;
     return threadIdx.x == 0;
 }
 

@@ -44,14 +44,18 @@ namespace {
 
 using namespace dev;
 
-// Resident warps per SM the register budget is cut for: 40 warps (48 registers)
-// for the plain steps and 36 warps (56 registers) for the reduction step, the
-// most that compile without spills (48 warps at 40 registers spill, and run
-// slower; the reduction step at 32 warps ran 5 % slower than at 36). The step
-// is bound by the latency of its global loads.
-template <int BX, bool REDUCE, bool OM1>
+// Resident warps per SM the register budget is cut for, the most that compile
+// without spills: 40 warps (48 registers) for the plain steps (48 warps at 40
+// registers spill, and run slower) and for the FP32 reduction step, whose
+// energy/mass accumulators then live in shared memory (sacc; 0.900 ms at
+// 8192^2 against 0.906 ms at 36 warps with register accumulators); 36 warps
+// (56 registers, register accumulators) for the FP16 reduction step, which is
+// bound by instruction issue and runs faster without the shared-memory traffic.
+// The FP32 step is bound by the latency of its global loads.
+template <typename T, bool REDUCE>
 struct StepWarps {
-    static constexpr int value = REDUCE ? 36 : 40;
+    static constexpr bool sacc = REDUCE && sizeof(T) == 4;
+    static constexpr int value = REDUCE && !sacc ? 36 : 40;
 };
 
 // Advance a row offset (row * stride, periodic over `total`) by one row in
@@ -73,10 +77,10 @@ __device__ __forceinline__ int step_row(int off, int stride, int total)
 // row reach it at about the same time and the second read hits L2. With
 // REDUCE, v receives this thread's FP64 partial sums {E_s, E_m, E_bulk, sum of
 // rho - rho_ref} of state t over its sites.
-template <typename T, int BX, bool REDUCE, bool OM1, bool MIRROR, int DIR>
+template <typename T, int BX, bool REDUCE, bool OM1, bool MIRROR, bool SACC, int DIR>
 __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int by, double v[4],
                                               float (*win)[BX + 4], float4 (*exR)[BX + 2],
-                                              float4 (*exL)[BX + 2], double* eacc)
+                                              float4 (*exL)[BX + 2], double* eacc, float* sacc)
 {
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
@@ -126,13 +130,18 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
     // (G+ + G0) + G- whatever the direction: hb = ahead-group sum of the behind
     // row, zb = zero-group sum of the behind row, hc = ahead-group sum of row r.
     float hb = 0.f, zb = 0.f, hc = 0.f;
-    // energy/mass sums: FP32 in registers for up to 64 rows, then added into this
-    // thread's FP64 slots in shared memory (eacc[q * BX + tid]), which keeps the
-    // FP64 accumulators out of the registers of the row loop
+    // energy/mass sums: FP32 for up to 64 rows, then added into FP64 slots of this
+    // thread in shared memory (eacc[q BX + tid]), which keeps the FP64 accumulators
+    // out of the registers of the row loop. With SACC the FP32 accumulators are
+    // shared-memory slots too (sacc), so that the FP32 reduction step fits the
+    // plain step's 48 registers and 40 warps per SM; otherwise registers.
     float es = 0.f, em = 0.f, eb = 0.f, ms = 0.f;
     if (REDUCE) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) eacc[q * BX + tid] = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            eacc[q * BX + tid] = 0.0;
+            if (SACC) sacc[q * BX + tid] = 0.f;
+        }
     }
 
     for (int k = 0; k <= nrows + 1; ++k) {
@@ -158,10 +167,21 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
         const bool out_site = out_col && k >= 1 && k <= nrows;
         float Sx, Sy;
         // the force, and on reduction steps the Sec. 5 energies of state t at (x, r)
+        if (SACC) {
+            es = sacc[0 * BX + tid];
+            em = sacc[1 * BX + tid];
+            eb = sacc[2 * BX + tid];
+        }
         force_energy<REDUCE>(rows, a, Sx, Sy, out_site ? 1.f : 0.f, pc, es, em, eb);
+        if (SACC) {
+            sacc[0 * BX + tid] = es;
+            sacc[1 * BX + tid] = em;
+            sacc[2 * BX + tid] = eb;
+        }
         float gs[9];
         const float d = collide<OM1>(f, -pc * Sx, -pc * Sy, a, gs);
-        if (REDUCE) ms = fmaf(out_site ? 1.f : 0.f, d, ms);
+        if (SACC) sacc[3 * BX + tid] = fmaf(out_site ? 1.f : 0.f, d, sacc[3 * BX + tid]);
+        else if (REDUCE) ms = fmaf(out_site ? 1.f : 0.f, d, ms);
 
         // ---- exchange post-collision values with the neighbouring columns
         exR[r & 1][tid + 1] = make_float4(gs[8], gs[1], gs[5], 0.f);
@@ -225,16 +245,30 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
         for (int i = 0; i < 9; ++i) f[i] = fn[i];
         if (REDUCE) {
             if ((k & 63) == 63) {
-                eacc[0 * BX + tid] += es;
-                eacc[1 * BX + tid] += em;
-                eacc[2 * BX + tid] += eb;
-                eacc[3 * BX + tid] += ms;
-                es = em = eb = ms = 0.f;
+                if (SACC) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        eacc[q * BX + tid] += sacc[q * BX + tid];
+                        sacc[q * BX + tid] = 0.f;
+                    }
+                } else {
+                    eacc[0 * BX + tid] += es;
+                    eacc[1 * BX + tid] += em;
+                    eacc[2 * BX + tid] += eb;
+                    eacc[3 * BX + tid] += ms;
+                    es = em = eb = ms = 0.f;
+                }
             }
         }
     }
 
     if (REDUCE) {
+        if (SACC) {
+            es = sacc[0 * BX + tid];
+            em = sacc[1 * BX + tid];
+            eb = sacc[2 * BX + tid];
+            ms = sacc[3 * BX + tid];
+        }
         v[0] = eacc[0 * BX + tid] + es;
         v[1] = eacc[1 * BX + tid] + em;
         v[2] = eacc[2 * BX + tid] + eb;
@@ -251,33 +285,53 @@ __device__ __forceinline__ void step_tile_dir(const StepArgs<T>& a, int bx, int 
 // bit-identical to that run's. MIRROR: the ring's stencil rows from one base
 // address (single-lattice plain steps; the reduction and batch kernels keep
 // the 8-slot ring, measured faster there).
-template <typename T, int BX, bool REDUCE, bool OM1, bool ALTERNATE, bool MIRROR>
+template <typename T, int BX, bool REDUCE, bool OM1, bool ALTERNATE, bool MIRROR, bool SACC>
 __device__ __forceinline__ void step_tile(const StepArgs<T>& a, int bx, int by, double v[4],
-                                          bool alternate = true)
+                                          double* eacc, bool alternate = true)
 {
     __shared__ float win[MIRROR ? 12 : 8][BX + 4];   // dpsi(t) rows, slot = row & 7
     __shared__ float4 exR[2][BX + 2];        // right-moving f*: speeds 8, 1, 5 (cy = -1, 0, +1)
     __shared__ float4 exL[2][BX + 2];        // left-moving f*: speeds 7, 3, 6
-    __shared__ double eacc[REDUCE ? 4 * BX : 1];   // FP64 energy/mass slots of the threads
+    __shared__ float sacc[SACC ? 4 * BX : 1];      // FP32 energy/mass slots of the threads
     if (ALTERNATE && alternate && (by & 1))
-        step_tile_dir<T, BX, REDUCE, OM1, MIRROR, -1>(a, bx, by, v, win, exR, exL, eacc);
+        step_tile_dir<T, BX, REDUCE, OM1, MIRROR, SACC, -1>(a, bx, by, v, win, exR, exL, eacc, sacc);
     else
-        step_tile_dir<T, BX, REDUCE, OM1, MIRROR, +1>(a, bx, by, v, win, exR, exL, eacc);
+        step_tile_dir<T, BX, REDUCE, OM1, MIRROR, SACC, +1>(a, bx, by, v, win, exR, exL, eacc, sacc);
 }
 
 template <typename T, int BX, bool REDUCE, bool OM1>
-__global__ void __launch_bounds__(BX, StepWarps<BX, REDUCE, OM1>::value * 32 / BX)
+__global__ void __launch_bounds__(BX, StepWarps<T, REDUCE>::value * 32 / BX)
     k_step(const StepArgs<T> a, bool alternate)
 {
+    __shared__ double eacc[REDUCE ? 4 * BX : 1];   // FP64 energy/mass slots, then the block sums
     double v[4];
-    step_tile<T, BX, REDUCE, OM1, true, !REDUCE>(a, blockIdx.x, blockIdx.y, v, alternate);
+    step_tile<T, BX, REDUCE, OM1, true, !REDUCE, StepWarps<T, REDUCE>::sacc>(a, blockIdx.x, blockIdx.y,
+                                                                              v, eacc, alternate);
     if (REDUCE) {
-        const unsigned int nb = gridDim.x * gridDim.y;
-        if (last_block_total<BX>(v, a.partials, a.counter, nb)) {
-            const double mass = (double)a.N * (double)a.rho_ref + v[3];
-            write_trace_row(a.trace, a.trace_count, a.t, mass, v[0], v[1], v[2]);
-            if (!isfinite(mass) || !isfinite(v[0]) || !isfinite(v[1])) atomicOr(a.err, 2);
+        // the CTA partial; k_step_total forms the grid sum and the trace row
+        block_sum4<BX>(v, eacc);
+        if (threadIdx.x == 0) {
+            double* p = a.partials + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) p[k] = v[k];
         }
+    }
+}
+
+// The grid sum of a reduction step of k_step (grid nbx x nby, launched after
+// it on the same stream): one CTA per CTA row, row_then_total, then the trace
+// row of state t. The row totals follow the CTA partials in a.partials.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_step_total(const StepArgs<T> a, int nbx)
+{
+    __shared__ double red[4 * NT];
+    const int nby = gridDim.x;
+    double* rows = a.partials + 4 * (size_t)nbx * nby;
+    double w[4];
+    if (row_then_total<NT>(a.partials, nbx, nby, blockIdx.x, rows, a.counter, w, red)) {
+        const double mass = (double)a.N * (double)a.rho_ref + w[3];
+        write_trace_row(a.trace, a.trace_count, a.t, mass, w[0], w[1], w[2]);
+        if (!isfinite(mass) || !isfinite(w[0]) || !isfinite(w[1])) atomicOr(a.err, 2);
     }
 }
 
@@ -301,15 +355,16 @@ __global__ void __launch_bounds__(BX, (REDUCE ? 28 : ALTERNATE ? 36 : 40) * 32 /
                  double* __restrict__ tile_partials)
 {
     __shared__ StepArgs<T> sa;
+    __shared__ double eacc[REDUCE ? 4 * BX : 1];   // FP64 energy/mass slots, then the block sum
     for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
         const int4 tl = tiles[k];                   // (replica, strip, chunk, alternate)
         __syncthreads();                            // previous tile done with sa and smem rings
         if (threadIdx.x == 0) sa = args[tl.x];
         __syncthreads();
         double v[4];
-        step_tile<T, BX, REDUCE, OM1, ALTERNATE, false>(sa, tl.y, tl.z, v, tl.w != 0);
+        step_tile<T, BX, REDUCE, OM1, ALTERNATE, false, false>(sa, tl.y, tl.z, v, eacc, tl.w != 0);
         if (REDUCE) {
-            block_sum4<BX>(v);
+            block_sum4<BX>(v, eacc);
             if (threadIdx.x == 0) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) tile_partials[4 * (size_t)k + q] = v[q];
@@ -318,22 +373,23 @@ __global__ void __launch_bounds__(BX, (REDUCE ? 28 : ALTERNATE ? 36 : 40) * 32 /
     }
 }
 
-// One CTA per replica: the replica's tile partials (tiles first .. first+n-1,
-// in the replica's own CTA order) summed like last_block_total, then one trace
-// row (t = rows already written x trace_every) into the replica's trace ring.
-template <int BX>
-__global__ void __launch_bounds__(BX)
-    k_batch_reduce(const double* __restrict__ tile_partials, const BatchRep* __restrict__ reps,
-                   int trace_every)
+// The grid sums of a batch's reduction step: one CTA per (replica, row chunk)
+// (rowmap), row_then_total over the replica's tile partials (tiles first ..
+// first + ntiles - 1, in the replica's own CTA order), exactly as k_step_total
+// sums k_step's CTA partials; then one trace row (t = rows already written x
+// trace_every) into the replica's trace ring.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+    k_batch_reduce(double* __restrict__ tile_partials, const BatchRep* __restrict__ reps,
+                   const int2* __restrict__ rowmap, int trace_every)
 {
-    const BatchRep r = reps[blockIdx.x];
-    double w[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int j = threadIdx.x; j < r.ntiles; j += BX) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] += tile_partials[4 * (size_t)(r.first_tile + j) + q];
-    }
-    block_sum4<BX>(w);
-    if (threadIdx.x == 0) {
+    __shared__ double red[4 * NT];
+    const int2 m = rowmap[blockIdx.x];            // (replica, row chunk)
+    const BatchRep r = reps[m.x];
+    const int nty = r.ntiles / r.ntx;
+    double w[4];
+    if (row_then_total<NT>(tile_partials + 4 * (size_t)r.first_tile, r.ntx, nty, m.y,
+                           tile_partials + 4 * (size_t)r.first_row, r.counter, w, red)) {
         const double mass = (double)r.N * r.rho_ref + w[3];
         const long long t = (long long)(*r.trace_count) * trace_every;
         write_trace_row(r.trace, r.trace_count, t, mass, w[0], w[1], w[2]);
@@ -489,6 +545,8 @@ cudaError_t launch_step_bx(const StepArgs<T>& a, Fp32Launch L, bool reduce, cuda
     if (reduce) {
         if (om1) k_step<T, BX, true, true><<<grid, BX, 0, s>>>(a, alt);
         else k_step<T, BX, true, false><<<grid, BX, 0, s>>>(a, alt);
+        if (cudaPeekAtLastError() != cudaSuccess) return cudaGetLastError();
+        k_step_total<T, BX><<<grid.y, BX, 0, s>>>(a, (int)grid.x);
     } else {
         if (om1) k_step<T, BX, false, true><<<grid, BX, 0, s>>>(a, alt);
         else k_step<T, BX, false, false><<<grid, BX, 0, s>>>(a, alt);
@@ -558,7 +616,7 @@ cudaError_t launch_batch_bx(const BatchLaunch<T>& b, bool reduce, cudaStream_t s
                       : pick(k_step_batch<T, BX, false, false, false>);
     }
     if (e != cudaSuccess || !reduce) return e;
-    k_batch_reduce<BX><<<b.nreps, BX, 0, s>>>(b.tile_partials, b.reps, b.trace_every);
+    k_batch_reduce<BX><<<b.nrows, BX, 0, s>>>(b.tile_partials, b.reps, b.rowmap, b.trace_every);
     return cudaGetLastError();
 }
 

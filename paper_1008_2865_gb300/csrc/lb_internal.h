@@ -100,8 +100,8 @@ struct StepArgs {
     float rho_ref, psi_ref, cpsi, inv_rho0;  // dpsi = cpsi * expm1(-(rho-rho_ref)/rho0)
     // energy/mass reduction (REDUCE launches only)
     float K0, half_A1;
-    double* partials;                // [gridDim.x*gridDim.y][4]
-    unsigned int* counter;           // arrival counter for the last-block reduction
+    double* partials;                // [gridDim.x*gridDim.y + gridDim.y][4]: CTA, row totals
+    unsigned int* counter;           // arrival counter of the last-block reductions
     double* trace;                   // [kTraceCap][5] ring
     int* trace_count;                // rows ever written
     long long t;                     // time level of the reduced state
@@ -135,6 +135,9 @@ inline bool marches_alternate(long long n) { return n * 80 > (128LL << 20); }
 // each replica's own CTA order; reps[r] locates replica r's tiles and its trace ring.
 struct BatchRep {
     int first_tile, ntiles;
+    int ntx;                   // tiles per row chunk
+    int first_row;             // slot of the replica's row totals (after all tile partials)
+    unsigned int* counter;     // the replica's arrival counter (its state's, zero between uses)
     long long N;
     double rho_ref;
     double* trace;
@@ -146,9 +149,11 @@ struct BatchLaunch {
     const StepArgs<T>* args;   // [nreps] arguments of this step's parity
     const int4* tiles;
     int ntiles;
-    double* tile_partials;     // [ntiles][4]
+    double* tile_partials;     // [ntiles + row chunks of all replicas][4]
     const BatchRep* reps;
     int nreps;
+    const int2* rowmap;        // [nrows] (replica, row chunk) of each reduction CTA
+    int nrows;
     int block_x;
     bool om1;                  // every replica has omega == 1
     int trace_every;
@@ -222,6 +227,7 @@ struct lb_state {
     // reductions, trace, scratch
     double* partials = nullptr;
     size_t partials_cap = 0;       // number of 4-double partials
+    int max_cta_rows = 0;          // CTA rows of the step's grid at most (kMinRows-row chunks)
     unsigned int* counter = nullptr;
     double* trace = nullptr;
     int* trace_count = nullptr;
