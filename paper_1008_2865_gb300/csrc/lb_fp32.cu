@@ -355,11 +355,22 @@ __global__ void __launch_bounds__(BX, (REDUCE ? 28 : ALTERNATE ? 36 : 40) * 32 /
                  double* __restrict__ tile_partials)
 {
     __shared__ StepArgs<T> sa;
+    __shared__ int sa_rep;                          // replica whose arguments sa holds
     __shared__ double eacc[REDUCE ? 4 * BX : 1];   // FP64 energy/mass slots, then the block sum
+    static_assert(sizeof(StepArgs<T>) % 4 == 0 && sizeof(StepArgs<T>) <= 4 * 96, "args copy");
+    // CTA c takes the consecutive items [c m, c m + m), m = ceil(ntiles / gridDim.x):
+    // neighbouring tiles of one replica, whose arguments then stay in sa
+    if (threadIdx.x == 0) sa_rep = -1;
     for (int k = blockIdx.x; k < ntiles; k += gridDim.x) {
         const int4 tl = tiles[k];                   // (replica, strip, chunk, alternate)
         __syncthreads();                            // previous tile done with sa and smem rings
-        if (threadIdx.x == 0) sa = args[tl.x];
+        if (threadIdx.x < 32 && tl.x != sa_rep) {   // warp 0 copies the arguments, 4 B a lane
+            const int* src = reinterpret_cast<const int*>(args + tl.x);
+            int* dst = reinterpret_cast<int*>(&sa);
+            for (int w = threadIdx.x; w < (int)(sizeof(StepArgs<T>) / 4); w += 32) dst[w] = __ldg(src + w);
+            __syncwarp();
+            if (threadIdx.x == 0) sa_rep = tl.x;
+        }
         __syncthreads();
         double v[4];
         step_tile<T, BX, REDUCE, OM1, ALTERNATE, false, false>(sa, tl.y, tl.z, v, eacc, tl.w != 0);
