@@ -32,9 +32,10 @@
 //      rho(t+1); the row behind r is then complete and its dpsi(t+1) is written.
 // One __syncthreads per row orders the exchange and the ring updates.
 // REDUCE launches also accumulate mass and the Sec. 5 pseudo-energies of
-// state t (FP32 per thread for 64 rows, then FP64), reduce them per CTA in
-// FP64 and let the last CTA to finish sum all CTA partials in a fixed order
-// into one trace row — deterministic for a given launch shape.
+// state t (FP32 per thread for 64 rows, then FP64) and reduce them per CTA in
+// FP64; k_step_total then sums the CTA partials, row by row and then the row
+// totals, in a fixed order into one trace row — deterministic for a given
+// launch shape.
 #include "lb_device.cuh"
 
 #include <cmath>
@@ -344,8 +345,8 @@ __global__ void __launch_bounds__(NT) k_step_total(const StepArgs<T> a, int nbx)
 // replica alternates; ALTERNATE: some replica does, and its kernels get a
 // 36-warp register budget). With REDUCE each tile's CTA partial (the same block
 // sum k_step forms) goes to tile_partials; k_batch_reduce then sums a
-// replica's partials in the order k_step's last CTA uses, so a replica's
-// fields and trace are bit-identical to running it alone with the same shape.
+// replica's partials in the order k_step_total uses, so a replica's fields
+// and trace are bit-identical to running it alone with the same shape.
 // (Measured on the 96-replica sweep and not kept: tiles handed out by an
 // atomic counter, 1.2% slower; alternating march directions for replicas that
 // fit in L2, no gain.)

@@ -101,7 +101,7 @@ struct StepArgs {
     // energy/mass reduction (REDUCE launches only)
     float K0, half_A1;
     double* partials;                // [gridDim.x*gridDim.y + gridDim.y][4]: CTA, row totals
-    unsigned int* counter;           // arrival counter of the last-block reductions
+    unsigned int* counter;           // arrival counter of the grid sums (zero between uses)
     double* trace;                   // [kTraceCap][5] ring
     int* trace_count;                // rows ever written
     long long t;                     // time level of the reduced state
