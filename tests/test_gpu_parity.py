@@ -527,3 +527,21 @@ def test_init_input_may_be_reused_at_once():
             got = lat.fields()
         for u, v in zip(got, ref[:3]):
             assert np.array_equal(u, v), where
+
+
+@pytest.mark.parametrize("nx,ny,launch", [(130, 2000, (64, 4, 0)), (61, 997, (64, 5, 0)),
+                                          (4000, 9, (256, 4, 0))])
+def test_reduction_grid_sum_shapes(nx, ny, launch):
+    """The reduction step's grid sum (one CTA per row of step CTAs, then the row totals)
+    on grids of many short CTA rows (500 and 200 rows of 3 and 1 CTAs) and of few long ones
+    (3 rows of 16 CTAs): trace and mass against the oracle, and the same trace bit for bit
+    from a second run."""
+    rho0 = inputs.noisy_density(nx, ny, seed=31, mean=0.7, amp=0.01, mode="rel")
+    ref = oracle.run(rho0, 30, G1=-5.0, G2=0.6, trace_every=10)
+    rho, ux, uy, tr, _ = _run_gpu(rho0, 30, launch=launch, G1=-5.0, G2=0.6, trace_every=10)
+    assert len(tr) == 3 and np.array_equal(tr[:, 0], ref[3][:, 0])
+    assert np.max(np.abs(tr[:, 1] - ref[3][:, 1]) / ref[3][:, 1]) <= 1e-6
+    assert _trace_err(tr, ref[3]) <= 1e-4
+    assert _norm_err(rho, ref[0]) <= 1e-5
+    tr2 = _run_gpu(rho0, 30, launch=launch, G1=-5.0, G2=0.6, trace_every=10)[3]
+    assert np.array_equal(tr, tr2)
