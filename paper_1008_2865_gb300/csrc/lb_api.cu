@@ -588,7 +588,7 @@ struct SavedHeader {
     double rho_ref;
     long long payload;        // bytes after the header
 };
-constexpr int kSaveVersion = 3;   // 3: tiled populations of state t (FP32 pairs side by side)
+constexpr int kSaveVersion = 4;   // 4: tiled populations of state t (pairs side by side, FP16 too)
 
 size_t payload_bytes(const lb_state* s)
 {

@@ -67,10 +67,10 @@ struct Tile<float> {   // paired: a pair is two adjacent elements
     static constexpr int A13 = 96, B13 = 97, A56 = 160, B56 = 161, A78 = 224, B78 = 225;
 };
 template <>
-struct Tile<__half> {  // nine runs of 32: population i at 32 i
-    static constexpr bool kPaired = false;
-    static constexpr int P0 = 0, P2 = 64, P4 = 128;
-    static constexpr int A13 = 32, B13 = 96, A56 = 160, B56 = 192, A78 = 224, B78 = 256;
+struct Tile<__half> {  // the same element offsets: a pair is one 4-byte access
+    static constexpr bool kPaired = true;
+    static constexpr int P0 = 0, P2 = 32, P4 = 64;
+    static constexpr int A13 = 96, B13 = 97, A56 = 160, B56 = 161, A78 = 224, B78 = 225;
 };
 __device__ __forceinline__ int tsingle(int x) { return (x >> 5) * kTileElems + (x & (kTileW - 1)); }
 template <typename T>
